@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched NTT on GB300.
+
+Default workload (one "step" = forward then inverse transform of every vector,
+lazy butterflies of Algorithms 3 and 4):
+    p = 998244353 (beta = 2^32), 64 transforms of L = 2^16, one of L = 2^20
+    and one of L = 2^22, uint32 residues uniform in [0, p) from a seed.
+The three groups run on three CUDA streams; every pass is one kernel launch
+timed with CUDA events on its own stream.  L2 is flushed (a 512 MiB write)
+between timed steps.  The NTL-style comparator (Algorithm 2 butterflies, same
+schedule) is timed the same way.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload c2|c1|c3|c4|c5]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica on its own GPU (the workload has no exchange step), value = total
+butterflies of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1205_2926_gb300.inputs import P_NTT30, P_NTT62, batch_inputs, uneven_batch_spec, uniform_residues  # noqa
+
+METRIC = "NTT butterflies/s & HBM GB/s, lazy vs NTL-style on GB300; p50/p99 polymul latency"
+
+WORKLOADS = {
+    "c1": {"name": "single forward+inverse NTT, L=2^10, p=998244353 (uint32)", "groups": [(P_NTT30, 10, 1)]},
+    "c2": {"name": "32-bit batched NTT, p=998244353: 64 x 2^16 + 1 x 2^20 + 1 x 2^22, forward+inverse",
+           "groups": [(P_NTT30, 16, 64), (P_NTT30, 20, 1), (P_NTT30, 22, 1)]},
+    "c3": {"name": "64-bit NTT, p=2305843009448574977: 16 x 2^20 + 1 x 2^24, forward+inverse",
+           "groups": [(P_NTT62, 20, 16), (P_NTT62, 24, 1)]},
+}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2070))}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed loop runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0: float, t1: float):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [ln for (t, ln) in self.lines if t0 - 0.15 <= t <= t1 + 0.15] or [ln for _, ln in self.lines]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in rows:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def butterflies(groups):
+    """Butterflies per forward (or inverse) transform set: l * L/2 per vector (Section 5 count)."""
+    return sum(b * l * (1 << l) // 2 for (_, l, b) in groups)
+
+
+def useful_bytes(groups):
+    """One read and one write of every word per transform."""
+    return sum(2 * b * (1 << l) * (4 if p < (1 << 30) else 8) for (p, l, b) in groups)
+
+
+# --------------------------------------------------------------------------- ours
+
+class GPUWorkload:
+    def __init__(self, groups, torch, ntt, seed=1):
+        self.torch, self.ntt = torch, ntt
+        self.groups = groups
+        self.plans, self.bufs, self.streams, self.host = [], [], [], []
+        for gi, (p, l, b) in enumerate(groups):
+            L = 1 << l
+            plan = ntt.ntt_plan(p, ntt.root_of_unity(p, L), L)
+            a = batch_inputs(seed + gi, b, L, p)
+            view = a.view(np.int32) if a.dtype == np.uint32 else a.view(np.int64)
+            t = torch.from_numpy(view.copy()).cuda()
+            self.plans.append(plan)
+            self.bufs.append(t)
+            self.streams.append(torch.cuda.Stream())
+            self.host.append(torch.from_numpy(view.copy()).pin_memory())
+        self.nsteps = [p.info().n_passes for p in self.plans]
+        self.flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def set_variant(self, v):
+        for p in self.plans:
+            p.set_variant(v)
+
+    def flush_l2(self):
+        self.flush_buf.fill_(1)
+
+    def step(self, events=None):
+        """Forward then inverse of every group, each pass a launch on the group's stream."""
+        torch, ntt = self.torch, self.ntt
+        cur = torch.cuda.current_stream()
+        for gi, (plan, buf, s) in enumerate(zip(self.plans, self.bufs, self.streams)):
+            s.wait_stream(cur)
+            b = self.groups[gi][2]
+            for inv in (0, 1):
+                for k in range(self.nsteps[gi]):
+                    if events is not None:
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(s)
+                    ntt.ntt_execute_step(plan, inv, k, buf, b, stream=s)
+                    if events is not None:
+                        e1.record(s)
+                        events.append(((gi, inv, k), e0, e1))
+        for s in self.streams:
+            cur.wait_stream(s)
+
+    def step_e2e(self):
+        """Host->device copy, forward, inverse, device->host copy, per group (pinned memory)."""
+        torch, ntt = self.torch, self.ntt
+        cur = torch.cuda.current_stream()
+        for gi, (plan, buf, s, h) in enumerate(zip(self.plans, self.bufs, self.streams, self.host)):
+            s.wait_stream(cur)
+            with torch.cuda.stream(s):
+                buf.copy_(h, non_blocking=True)
+                ntt.ntt_forward_batch(plan, buf, self.groups[gi][2], stream=s)
+                ntt.ntt_inverse_batch(plan, buf, self.groups[gi][2], stream=s)
+                h.copy_(buf, non_blocking=True)
+        for s in self.streams:
+            cur.wait_stream(s)
+
+
+def barrier(dist):
+    if dist is not None and dist.is_initialized():
+        dist.barrier()
+
+
+def time_steps(wl, torch, K, W, dist, with_events=False):
+    for _ in range(W):
+        wl.flush_l2()
+        wl.step()
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    per_step = []
+    events = []
+    t0 = time.time()
+    for _ in range(K):
+        wl.flush_l2()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        wl.step(events if with_events else None)
+        s1.record()
+        per_step.append((s0, s1))
+    torch.cuda.synchronize()
+    t1 = time.time()
+    barrier(dist)
+    ms = sum(a.elapsed_time(b) for a, b in per_step)
+    return ms, events, (t0, t1)
+
+
+def time_e2e(wl, torch, K, W, dist):
+    for _ in range(W):
+        wl.step_e2e()
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        wl.step_e2e()
+        torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    barrier(dist)
+    return (t1 - t0) * 1e3
+
+
+def kernel_stats(events, groups):
+    """Average duration per pass (group, direction, step) and the dominant one."""
+    acc = {}
+    for key, e0, e1 in events:
+        acc.setdefault(key, []).append(e0.elapsed_time(e1))
+    stats = {}
+    for key, v in acc.items():
+        gi = key[0]
+        p, l, b = groups[gi]
+        w = 4 if p < (1 << 30) else 8
+        stats[key] = {"avg_ms": float(np.mean(v)), "launches": len(v), "total_ms": float(np.sum(v)),
+                      "bytes": 2 * b * (1 << l) * w}
+    dom = max(stats, key=lambda k: stats[k]["total_ms"])
+    return stats, dom
+
+
+def max_over_ranks(x, dist, torch):
+    if dist is None or not dist.is_initialized():
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_sample(groups, budget_s):
+    """Run the CPU oracle (Algorithm 1 and its inverse, fully reduced, one
+    core) on whole transforms of each group until the budget is spent.
+    Returns (butterflies, seconds, description)."""
+    import oracle
+    o = oracle.get()
+    done_bfly, t_used, parts = 0, 0.0, []
+    per_group = budget_s / len(groups)
+    for gi, (p, l, b) in enumerate(groups):
+        L = 1 << l
+        w = o.root_of_unity(p, L)
+        a = batch_inputs(1 + gi, 1, L, p).astype(np.uint64)
+        n, t_g = 0, 0.0
+        while t_g < per_group and n < b:
+            t0 = time.perf_counter()
+            y = o.ntt_ref(p, w, a)
+            o.intt_ref(p, w, y)
+            t_g += time.perf_counter() - t0
+            n += 1
+        done_bfly += n * 2 * l * L // 2
+        t_used += t_g
+        parts.append(f"{n} x 2^{l} fwd+inv")
+    return done_bfly, t_used, "; ".join(parts)
+
+
+def cpu_baseline_oracle(groups, budget_s=12.0):
+    bf, t, desc = cpu_sample(groups, budget_s)
+    return {"value": bf / t, "unit": "butterflies/s", "cores": 1, "kind": "oracle",
+            "sample": desc + f" of the same workload ({t:.1f} s, single thread)"}
+
+
+def run_ours(args, dist, rank, world):
+    import torch
+    import paper_1205_2926_gb300 as ntt
+    from paper_1205_2926_gb300 import build
+
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    spec = WORKLOADS[args.workload]
+    groups = spec["groups"]
+    wl = GPUWorkload(groups, torch, ntt)
+    peaks = load_peaks()
+    sampler = ClockSampler(local)
+    sampler.start()
+    bfly_step = 2 * butterflies(groups)
+    bytes_step = 2 * useful_bytes(groups)
+
+    wl.set_variant(0)
+    ms_lazy, events, (t0, t1) = time_steps(wl, torch, args.steps, args.warmup, dist, with_events=True)
+    clocks = sampler.stop(t0, t1)
+    ms_lazy = max_over_ranks(ms_lazy, dist, torch)
+    stats, dom = kernel_stats(events, groups)
+    wl.set_variant(1)
+    ms_ntl, _, _ = time_steps(wl, torch, args.steps, args.warmup, dist)
+    ms_ntl = max_over_ranks(ms_ntl, dist, torch)
+    wl.set_variant(0)
+    ms_e2e = time_e2e(wl, torch, max(3, min(args.steps, 50)), 2, dist)
+    k_e2e = max(3, min(args.steps, 50))
+    ms_e2e = max_over_ranks(ms_e2e, dist, torch)
+
+    K = args.steps
+    value = world * bfly_step * K / (ms_lazy / 1e3)
+    ntl_value = world * bfly_step * K / (ms_ntl / 1e3)
+    ds = stats[dom]
+    achieved = ds["bytes"] / (ds["avg_ms"] / 1e3) / 1e9
+    gi, inv, k = dom
+    p_, l_, b_ = groups[gi]
+    dom_name = f"{'inverse' if inv else 'forward'} pass {k} of {b_} x 2^{l_}"
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "butterflies/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": ms_lazy / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32" if groups[0][0] < (1 << 30) else "u64",
+        "data": "synthetic (seeded uniform residues)",
+        "config": {"workload": spec["name"], "butterflies_per_step": bfly_step,
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+        "hbm_gbs_useful": world * bytes_step * K / (ms_lazy / 1e3) / 1e9,
+        "ntl": {"value": ntl_value, "unit": "butterflies/s", "ms_per_step": ms_ntl / K},
+        "lazy_over_ntl": ms_ntl / ms_lazy,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": dom_name, "peak_src": peaks["src"]},
+        "kernels": {f"g{g}{'i' if i else 'f'}{s}": round(v["avg_ms"] * 1e3, 2) for (g, i, s), v in stats.items()},
+        "e2e": {"value": world * bfly_step * k_e2e / (ms_e2e / 1e3), "unit": "butterflies/s",
+                "h2d_bytes_per_step": useful_bytes(groups) // 2, "d2h_bytes_per_step": useful_bytes(groups) // 2},
+        "gpu_launches": len(events) // K,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_oracle(groups)
+    return line
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, same config, metric and unit.
+    Each step is a bounded sample of the workload (whole transforms)."""
+    if rank != 0:
+        return None
+    spec = WORKLOADS[args.workload]
+    groups = spec["groups"]
+    budget = max(0.5, min(6.0, 60.0 / max(args.steps + args.warmup, 1)))
+    for _ in range(args.warmup):
+        cpu_sample(groups, budget)
+    bf_total, t_total, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        bf, t, desc = cpu_sample(groups, budget)
+        bf_total += bf
+        t_total += t
+    value = bf_total / t_total
+    bfly_step = 2 * butterflies(groups)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "butterflies/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": bfly_step / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32" if groups[0][0] < (1 << 30) else "u64",
+        "data": "synthetic (seeded uniform residues)",
+        "config": {"workload": spec["name"], "butterflies_per_step": bfly_step},
+        "cpu_baseline": {"value": value, "unit": "butterflies/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: {desc} of the workload, single thread"},
+        "e2e": {"value": value, "unit": "butterflies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    line = run_ours(args, dist, rank, world)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,289 @@
+/*
+ * ntt_gb300.h -- C ABI of the GB300 (sm_103a) batched number-theoretic
+ * transform library.
+ *
+ * The transform (Harvey, "Faster arithmetic for number-theoretic transforms",
+ * arXiv:1205.2926, Section 1): for a word-sized prime p with p = 1 mod L,
+ * L = 2^l, and a primitive L-th root of unity omega,
+ *      b_j = sum_{i<L} omega^(i j) a_i  (mod p),   0 <= j < L,
+ * computed by the radix-2 schedule of Algorithm 1, whose output is in
+ * bit-reversed order: position k holds b_{rev_l(k)}.
+ *
+ * Arithmetic (Sections 2-4): butterflies use Shoup's product with a
+ * precomputed quotient W' = floor(W beta / p) and keep residues redundant,
+ * in [0, 2p) for the forward butterfly (Algorithm 3) and [0, 4p) for the
+ * inverse butterfly (Algorithm 4); one final reduction returns [0, p).  The
+ * fully reduced butterfly of Algorithm 2 is available as a comparison
+ * variant.  The word size beta follows from p:
+ *      p < 2^30  ->  beta = 2^32, data words are uint32_t;
+ *      p < 2^62  ->  beta = 2^64, data words are uint64_t.
+ * (Algorithms 3 and 4 need p < beta/4.)
+ *
+ * Conventions for every entry point:
+ *  - Return value: NTT_OK (0) or a negative NTT_ERR_* code; nothing throws and
+ *    nothing aborts.  ntt_strerror() names a code.
+ *  - Device pointers are CUDA device (or managed) memory on the device that
+ *    was current when the plan was made; the caller owns them.  They must be
+ *    16-byte aligned (NTT_ERR_ALIGN otherwise).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Transform calls are asynchronous on that stream: they return
+ *    after enqueueing, and errors of the kernels themselves surface at the
+ *    caller's next synchronisation.
+ *  - Plans own their device tables; a plan may be used from one host thread
+ *    at a time and by any number of streams (the tables are read-only).
+ */
+#ifndef NTT_GB300_H
+#define NTT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define NTT_OK 0
+#define NTT_ERR_MODULUS -1   /* p not prime, p >= 2^62, or p even */
+#define NTT_ERR_LENGTH -2    /* L not a power of two, L < 2, or L does not divide p-1 */
+#define NTT_ERR_ROOT -3      /* omega^L != 1 or omega^(L/2) != p-1 */
+#define NTT_ERR_ARG -4       /* null pointer, zero size, stride < L, bad enum */
+#define NTT_ERR_CUDA -5      /* a CUDA runtime call failed (see ntt_last_cuda_error) */
+#define NTT_ERR_NOMEM -6     /* device or host allocation failed */
+#define NTT_ERR_TIMEOUT -7   /* a bounded device-side wait gave up */
+#define NTT_ERR_ALIGN -8     /* pointer or stride not 16-byte aligned */
+#define NTT_ERR_RANGE -9     /* size beyond a documented maximum */
+#define NTT_ERR_REFUSED -10  /* server: request refused by admission (too large for the memory budget) */
+#define NTT_ERR_CANCELLED -11 /* server: request was cancelled */
+#define NTT_ERR_PENDING -12  /* server: request not finished yet */
+#define NTT_ERR_FAILED -13   /* server: request failed */
+
+/* Butterfly variants (ntt_plan_set_variant). */
+#define NTT_VARIANT_LAZY 0 /* Algorithms 3 (forward) and 4 (inverse), redundant residues */
+#define NTT_VARIANT_NTL 1  /* Algorithm 2 and its fully reduced inverse (comparison baseline) */
+
+typedef struct ntt_plan_s *ntt_plan_t;
+
+/* ---------------------------------------------------------- number theory */
+
+/* Deterministic Miller-Rabin test of n (bases: the first twelve primes, exact
+ * for every 64-bit n).  *is_prime receives 1 or 0.  Host only. */
+int ntt_is_prime(uint64_t n, int *is_prime);
+
+/* Section 1 fixes "one of" the primitive L-th roots; this library's choice is
+ * omega = g^((p-1)/L) with g the smallest quadratic non-residue mod p.
+ * Errors: NTT_ERR_MODULUS, NTT_ERR_LENGTH.  Host only. */
+int ntt_root_of_unity(uint64_t p, uint64_t L, uint64_t *omega);
+
+/* Smallest prime q > lo with q = 1 mod 2^k (deterministic search).  Host only. */
+int ntt_find_prime(uint64_t lo, int k, uint64_t *q);
+
+/* ------------------------------------------------------------------ plans */
+
+/* Make a plan for length-L transforms over F_p with root omega (Section 1).
+ * Validates p (prime, < 2^62), L (power of two, 2 <= L, L | p-1) and omega
+ * (omega^(L/2) = p-1, hence order exactly L), computes omega^-1 and L^-1, and
+ * uploads the twiddle tables (W, W') of Algorithm 3/4 for both directions to
+ * the current device.  *out receives the plan; the library owns its memory
+ * until ntt_plan_destroy.  The variant starts as NTT_VARIANT_LAZY.
+ * Errors: NTT_ERR_ARG, NTT_ERR_MODULUS, NTT_ERR_LENGTH, NTT_ERR_ROOT,
+ * NTT_ERR_RANGE (L > 2^26), NTT_ERR_NOMEM, NTT_ERR_CUDA. */
+int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L);
+
+/* Free a plan and its device tables (synchronises the device first). */
+int ntt_plan_destroy(ntt_plan_t plan);
+
+/* Select NTT_VARIANT_LAZY or NTT_VARIANT_NTL for later calls on this plan. */
+int ntt_plan_set_variant(ntt_plan_t plan, int variant);
+
+/* Read-only description of a plan.  word_bytes is 4 or 8; n_passes is the
+ * number of on-chip passes the transform is split into (four-step split of
+ * Algorithm 1's stages); log_r[i] is log2 of pass i's sub-transform length;
+ * table_bytes counts the plan's device tables. */
+typedef struct {
+    uint64_t p, omega, omega_inv, L, L_inv;
+    int log_L, word_bytes, variant, n_passes;
+    int log_r[4];
+    uint64_t table_bytes;
+} ntt_plan_info_t;
+int ntt_plan_get_info(ntt_plan_t plan, ntt_plan_info_t *info);
+
+/* Override the pass split (autotuning; n_passes 1..4, sum of log_r = log L,
+ * every log_r[i] in [3, 12], column passes (all but the last) at most 10 and
+ * followed by at least 2^5 (32-bit words) or 2^4 (64-bit words) elements).
+ * Rebuilds the plan's middle-twiddle tables.  NTT_ERR_ARG if the split is not
+ * allowed. */
+int ntt_plan_set_split(ntt_plan_t plan, int n_passes, const int *log_r);
+
+/* ------------------------------------------------------------- transforms */
+
+/* Forward transform of `batch` vectors in place (Section 1, Algorithm 1 with
+ * Algorithm 3 butterflies).  Vector b starts at word b*stride_words of d_data
+ * (words are uint32_t or uint64_t per the plan).  Input residues may lie in
+ * [0, 2p) for the lazy variant (Algorithm 3's input range) and must lie in
+ * [0, p) for NTT_VARIANT_NTL; the output is in [0, p), bit-reversed order.
+ * stride_words >= L and stride_words*word_bytes a multiple of 16.
+ * Errors: NTT_ERR_ARG, NTT_ERR_ALIGN, NTT_ERR_CUDA (launch failure). */
+int ntt_forward_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride_words, void *stream);
+
+/* Inverse transform in place: Algorithm 1 run backwards (Section 4) with the
+ * Algorithm 4 butterfly and the inverse root.  Input in bit-reversed order,
+ * residues in [0, 4p) (lazy) or [0, p) (NTL); output in natural order in
+ * [0, p), UNNORMALISED: inverse(forward(a)) = L * a.  Layout and errors as
+ * ntt_forward_batch. */
+int ntt_inverse_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride_words, void *stream);
+
+/* One execution step (one pass, one kernel launch) of a transform: steps
+ * 0 .. n_passes-1 run in order are exactly ntt_forward_batch (inverse = 0) or
+ * ntt_inverse_batch (inverse = 1); intermediate contents between steps are
+ * residues in the redundant range and in the four-step intermediate order.
+ * For profiling and per-kernel timing.  Errors as ntt_forward_batch, plus
+ * NTT_ERR_ARG for a step outside [0, n_passes). */
+int ntt_execute_step(ntt_plan_t plan, int inverse, int step, void *d_data, size_t batch, size_t stride_words,
+                     void *stream);
+
+/* Same transforms on HOST buffers: copies the batch to a device buffer owned
+ * by the plan (grown on demand), transforms it on `stream`, copies it back
+ * and synchronises the stream before returning.  `inverse` is 0 or 1.  For
+ * pinned host memory the copies are asynchronous DMA; any host memory works.
+ * Errors: as above plus NTT_ERR_NOMEM. */
+int ntt_transform_host(ntt_plan_t plan, int inverse, void *h_data, size_t batch, size_t stride_words,
+                       void *stream);
+
+/* ------------------------------------------------- polynomial products */
+
+/* c = a * b in F_p[x] (the polynomial-multiplication application, Section 1):
+ * zero-pad both operands to L = nextpow2(na + nb - 1), forward transforms,
+ * pointwise product times L^-1 (Montgomery reduction as in Algorithm 5, then
+ * a Shoup product by L^-1), inverse transform.  a, b, c are DEVICE arrays of
+ * natural-order coefficients in [0, p) in the word type of p; c receives
+ * na + nb - 1 words.  omega is the library's root for (p, L).  Plans are
+ * cached per (device, p, L); device scratch of 2*L words is allocated per
+ * call (stream-ordered) and released on the stream.  Asynchronous on `stream`.
+ * Errors: NTT_ERR_ARG (null, na or nb zero), NTT_ERR_LENGTH (L does not divide
+ * p-1), NTT_ERR_MODULUS, NTT_ERR_ALIGN, NTT_ERR_NOMEM, NTT_ERR_CUDA. */
+int polymul_mod_p(uint64_t p, const void *d_a, size_t na, const void *d_b, size_t nb, void *d_c, void *stream);
+
+/* ------------------------------------------------------------- uneven batch */
+
+/* One transform of an uneven batch: its plan, its device vector (L words of
+ * the plan's word type, 16-byte aligned) and its direction (0 forward,
+ * 1 inverse).  Plans may differ in p and L; all must use 32-bit words and the
+ * lazy variant, and live on the current device. */
+typedef struct {
+    ntt_plan_t plan;
+    void *d_data;
+    int inverse;
+} ntt_desc_t;
+
+/* Run every transform of `descs` in ONE persistent kernel launch: the work is
+ * cut into tiles of every pass of every transform, tiles are handed out by a
+ * device-side atomic counter in dependency order, and a tile of a later pass
+ * waits (bounded by a clock budget) for the tiles of the earlier pass of the
+ * same transform.  Results are those of ntt_forward_batch/ntt_inverse_batch
+ * on each transform alone.  Host-side preparation (descriptor upload) is
+ * cached: calling again with the same descs array contents reuses it, so
+ * the call can be captured in a CUDA graph after a first warm-up call.
+ * Errors: NTT_ERR_ARG, NTT_ERR_RANGE (a 64-bit or NTL plan, or L > 2^22),
+ * NTT_ERR_CUDA, NTT_ERR_TIMEOUT (reported by ntt_uneven_status when a wait
+ * gave up). */
+int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream);
+
+/* Status word of the last ntt_execute_uneven on this device, read after the
+ * stream has been synchronised: NTT_OK or NTT_ERR_TIMEOUT. */
+int ntt_uneven_status(int *status);
+
+/* Failure-detection hook for tests and operators: set the clock-cycle budget
+ * of every device-side wait of ntt_execute_uneven (default 2e9, about one
+ * second) and, when stall_stage >= 1, make every wait of that stage ask for
+ * one completion more than can ever arrive, so that the wait runs out and
+ * the launch ends with status NTT_ERR_TIMEOUT instead of hanging.
+ * stall_stage = -1 restores normal waits.  Takes effect at the next launch
+ * (a prepared batch keeps no copy of these values). */
+int ntt_uneven_set_wait_budget(long long cycles, int stall_stage);
+
+/* -------------------------------------------------- polymul serving loop */
+
+/* A continuous-batching server of polynomial products mod p (the Section 1
+ * application under a request stream).  A scheduler thread admits queued
+ * requests in FIFO order while their device memory (2 L words each) fits in
+ * mem_budget_bytes, groups them by L = nextpow2(na+nb-1), and runs each group
+ * as one batch (forward transforms of both operands, pointwise product times
+ * L^-1, inverse transform) on the next of n_streams CUDA streams.  Requests
+ * arriving while batches run are admitted as memory frees up, and their
+ * batches overlap with the running ones on the device.  Each result is the
+ * same as polymul_mod_p on that request alone. */
+typedef struct ntt_server_s *ntt_server_t;
+
+typedef struct {
+    uint64_t p;              /* prime modulus (word type as for plans) */
+    size_t max_coeffs;       /* largest accepted na or nb */
+    size_t mem_budget_bytes; /* device bytes for admitted, unfinished requests */
+    int n_streams;           /* concurrent CUDA streams, 1..64 */
+    int max_batch;           /* most requests of one length per batch */
+} ntt_server_config_t;
+
+typedef struct {
+    uint64_t completed, refused, cancelled, failed, batches;
+    double butterflies;                      /* transform butterflies of completed requests */
+    double p50_us, p99_us, mean_us, max_us;  /* submit-to-result latency of completed requests */
+    double wall_s;                           /* first submit to last completion */
+} ntt_server_stats_t;
+
+/* Start a server on the current device.  Errors: NTT_ERR_ARG, NTT_ERR_MODULUS,
+ * NTT_ERR_LENGTH (p has no root of order nextpow2(2*max_coeffs-1)),
+ * NTT_ERR_CUDA. */
+int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out);
+
+/* Queue c = a * b.  h_a, h_b, h_c are HOST arrays (na, nb and na+nb-1 words
+ * of the word type of p, coefficients in [0, p)) that must stay valid and
+ * untouched until the request finishes; pinned memory gives asynchronous
+ * copies.  *req_id receives the request id even when the request is refused.
+ * Returns NTT_OK, or NTT_ERR_REFUSED for a request too large for max_coeffs
+ * or the memory budget (or with a length p does not support), or NTT_ERR_ARG. */
+int ntt_server_submit(ntt_server_t sv, const void *h_a, size_t na, const void *h_b, size_t nb, void *h_c,
+                      uint64_t *req_id);
+
+/* Status of a request: NTT_ERR_PENDING (queued or running), NTT_OK (result
+ * written to h_c), NTT_ERR_REFUSED, NTT_ERR_CANCELLED or NTT_ERR_FAILED. */
+int ntt_server_poll(ntt_server_t sv, uint64_t req_id, int *status);
+
+/* Block until the request is no longer pending or timeout_ms passes (< 0:
+ * no limit); *status as ntt_server_poll. */
+int ntt_server_wait(ntt_server_t sv, uint64_t req_id, int timeout_ms, int *status);
+
+/* Cancel a request that is still queued (not yet admitted): NTT_OK; a request
+ * already admitted runs to completion and this returns NTT_ERR_PENDING. */
+int ntt_server_cancel(ntt_server_t sv, uint64_t req_id);
+
+/* Wait until nothing is queued or running (timeout_ms < 0: no limit);
+ * NTT_ERR_PENDING on timeout. */
+int ntt_server_drain(ntt_server_t sv, int timeout_ms);
+
+/* Counters and latency percentiles since creation or the last reset. */
+int ntt_server_stats(ntt_server_t sv, ntt_server_stats_t *out);
+int ntt_server_reset_stats(ntt_server_t sv);
+
+/* Failure injection on the host: the next n_batches batches fail before
+ * launch; their requests end NTT_ERR_FAILED and other batches are unaffected. */
+int ntt_server_inject_failures(ntt_server_t sv, int n_batches);
+
+/* Finish queued and running work, stop the scheduler, free the server. */
+int ntt_server_destroy(ntt_server_t sv);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Human-readable name of a status code (static storage). */
+const char *ntt_strerror(int code);
+
+/* The last CUDA error string seen by the library on this host thread. */
+const char *ntt_last_cuda_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int ntt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NTT_GB300_H */

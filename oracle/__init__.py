@@ -12,6 +12,7 @@ Functions and the passages they follow (Harvey, arXiv:1205.2926):
 
 * ``dft_naive`` / ``idft_naive``  -- Section 1 definition of the NTT, placed in
   Algorithm 1's bit-reversed order; the inverse of Section 4 (unnormalised).
+* ``dft_at`` -- one output position from the definition (O(L)).
 * ``ntt_ref`` / ``intt_ref``      -- Algorithm 1, and Algorithm 1 run backwards.
 * ``polymul_schoolbook`` / ``polymul_ntt`` -- the polynomial-multiplication
   application of Section 1 (definition, and the convolution theorem).
@@ -77,6 +78,7 @@ def _load(mutant: int = 0) -> ctypes.CDLL:
             ("or_intt_ref_batch", None, [_u64, _u64, _u64, _p64, _u64, _u64]),
             ("or_polymul_schoolbook", None, [_u64, _p64, _u64, _p64, _u64, _p64]),
             ("or_polymul_ntt", ctypes.c_int, [_u64, _p64, _u64, _p64, _u64, _p64]),
+            ("or_dft_at", _u64, [_u64, _u64, _u64, _p64, _u64]),
         ]:
             f = getattr(lib, name)
             f.restype = res
@@ -152,6 +154,11 @@ class Oracle:
         else:
             self.lib.or_intt_ref_batch(p, w, x.shape[1], _ptr(x), x.shape[0], x.shape[1])
         return x
+
+    def dft_at(self, p: int, w: int, a, k: int) -> int:
+        """Output position k of the forward transform (definition, O(L))."""
+        a = _as_u64(a)
+        return int(self.lib.or_dft_at(p, w, a.size, _ptr(a), k))
 
     def polymul_schoolbook(self, p: int, a, b) -> np.ndarray:
         a, b = _as_u64(a), _as_u64(b)

@@ -17,6 +17,7 @@
  * Functions (each cites the passage it follows):
  *   or_dft_naive     -- Section 1 definition b_j = sum_i w^{ij} a_i, placed in
  *                       bit-reversed order as Algorithm 1's output is.
+ *   or_dft_at        -- one output position of the definition, O(L).
  *   or_idft_naive    -- the definition of the inverse map used by running
  *                       Algorithm 1 backwards (Section 4): unnormalised.
  *   or_ntt_ref       -- Algorithm 1 (Section 1) with fully reduced arithmetic.
@@ -277,4 +278,18 @@ int or_polymul_ntt(uint64_t p, const uint64_t *a, uint64_t na, const uint64_t *b
     free(A);
     free(B);
     return 0;
+}
+
+/* One output position of the forward transform, straight from the Section 1
+ * definition: out[k] = b_{rev_l(k)} = sum_i w^(i rev_l(k)) a_i.  O(L); used to
+ * check sampled positions of transforms too large for a full comparison. */
+uint64_t or_dft_at(uint64_t p, uint64_t w, uint64_t L, const uint64_t *a, uint64_t k) {
+    int l = ilog2_exact(L);
+    uint64_t wj = or_powmod(w, or_bitrev(k, l), p);
+    uint64_t acc = 0, x = 1;
+    for (uint64_t i = 0; i < L; i++) {
+        acc = addmod(acc, mulmod(x, a[i], p), p);
+        x = mulmod(x, wj, p);
+    }
+    return acc;
 }

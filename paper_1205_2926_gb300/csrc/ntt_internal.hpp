@@ -1,0 +1,89 @@
+// ntt_internal.hpp -- host-side structures shared by the library's
+// translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "../../include/ntt_gb300.h"
+
+namespace ntt {
+
+constexpr int kMaxPasses = 4;
+constexpr int kMaxRowLog = 12;  // longest on-chip sub-transform of a row pass
+constexpr int kMaxColLog = 10;  // longest column-pass sub-transform
+
+// Host number theory (the library's own; independent of any test code).
+namespace nt {
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p);
+uint64_t powmod(uint64_t a, uint64_t e, uint64_t p);
+bool is_prime(uint64_t n);
+uint64_t smallest_qnr(uint64_t p);
+uint64_t shoup_quotient(uint64_t w, uint64_t p, int word_bits);  // floor(w * beta / p)
+uint32_t bitrev(uint32_t k, int bits);
+}  // namespace nt
+
+struct PassPlan {
+    int logR = 0;   // sub-transform length
+    int logS = 0;   // column stride (0: row pass)
+    int logTV = 3;  // column pass: 16-byte vectors per tile row
+    int logTA = 0;  // column pass: MA table width
+    bool has_mb = false;
+    void *ma[2] = {nullptr, nullptr};  // [direction] middle tables
+    void *mb[2] = {nullptr, nullptr};
+};
+
+}  // namespace ntt
+
+struct ntt_plan_s {
+    uint64_t p = 0, omega = 0, omega_inv = 0, L = 0, L_inv = 0;
+    int logL = 0;
+    int wbytes = 4;
+    int variant = NTT_VARIANT_LAZY;
+    int device = 0;
+    int npass = 0;
+    ntt::PassPlan pass[ntt::kMaxPasses];
+    void *tw[2] = {nullptr, nullptr};  // stage tables per direction
+    int tw_log = 0;                    // tables cover distances m < 2^tw_log
+    uint64_t table_bytes = 0;
+    // host-buffer staging (ntt_transform_host)
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    std::mutex mu;
+};
+
+namespace ntt {
+
+// Launch of one pass (kind: 0 column pass, 1 row pass, 2 tiny length 2/4).
+// Defined per word type in ntt_pass_u32.cu / ntt_pass_u64.cu.
+struct LaunchSpec {
+    void *data;
+    uint64_t stride;
+    uint32_t batch;
+    int logL, logR, logS, logTV, logTA;
+    int per_cta;
+    uint32_t flags;
+    const void *tw, *ma, *mb;
+    uint64_t p;
+    uint64_t nrows;
+    unsigned grid;
+    size_t smem;
+};
+cudaError_t launch_pass_u32(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
+cudaError_t launch_pass_u64(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
+
+// Enqueue a whole forward or inverse transform of a batch (all passes).
+int enqueue_transform(ntt_plan_s *plan, int dir, void *data, size_t batch, size_t stride, cudaStream_t st);
+
+// Enqueue execution steps first .. first+count-1 of a transform (a step is
+// one pass; the inverse executes the passes in reverse order).
+int enqueue_steps(ntt_plan_s *plan, int dir, void *data, size_t batch, size_t stride, cudaStream_t st, int first,
+                  int count);
+
+// Record a CUDA failure for ntt_last_cuda_error(); returns NTT_ERR_CUDA.
+int cuda_fail(cudaError_t e, const char *where);
+
+}  // namespace ntt

@@ -1,0 +1,518 @@
+// ntt_plan.cu -- host side of the library: number theory, plans and their
+// device tables, the pass schedule, and the transform entry points of the C ABI.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "ntt_internal.hpp"
+
+namespace ntt {
+
+static thread_local std::string g_last_cuda_error;
+
+int cuda_fail(cudaError_t e, const char *where) {
+    g_last_cuda_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return NTT_ERR_CUDA;
+}
+
+// ------------------------------------------------------------ number theory
+namespace nt {
+
+typedef unsigned __int128 u128;
+
+uint64_t mulmod(uint64_t a, uint64_t b, uint64_t p) { return (uint64_t)((u128)a * b % p); }
+
+uint64_t powmod(uint64_t a, uint64_t e, uint64_t p) {
+    uint64_t result = 1 % p, base = a % p;
+    while (e) {
+        if (e & 1) result = mulmod(result, base, p);
+        base = mulmod(base, base, p);
+        e >>= 1;
+    }
+    return result;
+}
+
+// Strong-probable-prime test to each of the first twelve prime bases; this
+// set has no 64-bit strong pseudoprime, so the answer is exact.
+bool is_prime(uint64_t n) {
+    const uint64_t small[12] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (uint64_t q : small) {
+        if (n % q == 0) return n == q;
+    }
+    uint64_t d = n - 1;
+    int s = __builtin_ctzll(d);
+    d >>= s;
+    for (uint64_t a : small) {
+        uint64_t x = powmod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool witness = true;
+        for (int i = 1; i < s && witness; ++i) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) witness = false;
+        }
+        if (witness) return false;
+    }
+    return true;
+}
+
+uint64_t smallest_qnr(uint64_t p) {
+    const uint64_t half = (p - 1) / 2;
+    for (uint64_t g = 2; g < p; ++g)
+        if (powmod(g, half, p) == p - 1) return g;
+    return 0;
+}
+
+uint64_t shoup_quotient(uint64_t w, uint64_t p, int word_bits) {
+    return (uint64_t)(((u128)w << word_bits) / p);
+}
+
+uint32_t bitrev(uint32_t k, int bits) {
+    uint32_t r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((k >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+
+}  // namespace nt
+
+// ------------------------------------------------------------ pass schedule
+
+static int ilog2u(uint64_t x) { return 63 - __builtin_clzll(x); }
+
+// Default split of log L into passes: one row pass of at most 2^12 elements,
+// preceded by as few column passes (each at most 2^10) as needed, balanced.
+static int default_split(int logL, int wbytes, int *logr) {
+    (void)wbytes;
+    if (logL <= kMaxRowLog) {
+        logr[0] = logL;
+        return 1;
+    }
+    if (logL <= 22) {
+        int c = std::max(logL - kMaxRowLog, std::min((logL + 1) / 2, 9));
+        logr[0] = c;
+        logr[1] = logL - c;
+        return 2;
+    }
+    int rest = logL - kMaxRowLog;  // two column passes
+    logr[0] = (rest + 1) / 2;
+    logr[1] = rest - logr[0];
+    logr[2] = kMaxRowLog;
+    return 3;
+}
+
+static bool split_ok(int logL, int wbytes, int n, const int *logr) {
+    if (n < 1 || n > kMaxPasses) return false;
+    if (logL <= 2) return n == 1 && logr[0] == logL;
+    int sum = 0;
+    const int logT = wbytes == 4 ? 5 : 4;  // narrowest column tile is 16 bytes; need S >= 8 vectors
+    for (int i = 0; i < n; ++i) {
+        if (logr[i] < 3 || logr[i] > kMaxRowLog) return false;
+        sum += logr[i];
+    }
+    if (sum != logL) return false;
+    int after = logL;
+    for (int i = 0; i < n - 1; ++i) {
+        after -= logr[i];
+        if (logr[i] > kMaxColLog) return false;
+        if (after < logT) return false;
+    }
+    return true;
+}
+
+// Widest column tile: 8 vectors (128-byte rows), or the whole column stride.
+static int max_logtv(int logS, int wbytes) {
+    const int logV = wbytes == 4 ? 2 : 1;
+    return std::min(3, logS - logV);
+}
+
+static void free_tables(ntt_plan_s *pl) {
+    for (int d = 0; d < 2; ++d) {
+        if (pl->tw[d]) cudaFree(pl->tw[d]);
+        pl->tw[d] = nullptr;
+        for (int q = 0; q < kMaxPasses; ++q) {
+            if (pl->pass[q].ma[d]) cudaFree(pl->pass[q].ma[d]);
+            if (pl->pass[q].mb[d]) cudaFree(pl->pass[q].mb[d]);
+            pl->pass[q].ma[d] = pl->pass[q].mb[d] = nullptr;
+        }
+    }
+    pl->table_bytes = 0;
+}
+
+// Upload a host vector of (W, W') pairs (as uint64) in the plan's word type.
+static int upload_pairs(ntt_plan_s *pl, const std::vector<uint64_t> &pairs, void **dst) {
+    const size_t n = pairs.size();
+    const size_t bytes = n * pl->wbytes;
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "cudaMalloc");
+    if (pl->wbytes == 4) {
+        std::vector<uint32_t> h(n);
+        for (size_t i = 0; i < n; ++i) h[i] = (uint32_t)pairs[i];
+        e = cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMemcpy(d, pairs.data(), bytes, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy tables");
+    }
+    *dst = d;
+    pl->table_bytes += bytes;
+    return NTT_OK;
+}
+
+static inline void push_pair(std::vector<uint64_t> &v, uint64_t w, uint64_t p, int bits) {
+    v.push_back(w);
+    v.push_back(nt::shoup_quotient(w, p, bits));
+}
+
+// Build every device table of the plan for its current split.
+static int build_tables(ntt_plan_s *pl) {
+    free_tables(pl);
+    const uint64_t p = pl->p;
+    const int bits = pl->wbytes * 8;
+    const int logV = pl->wbytes == 4 ? 2 : 1;
+    int maxr = 0;
+    for (int q = 0; q < pl->npass; ++q) maxr = std::max(maxr, pl->pass[q].logR);
+    pl->tw_log = std::max(1, maxr);
+    for (int d = 0; d < 2; ++d) {
+        const uint64_t root = d == 0 ? pl->omega : pl->omega_inv;
+        // stage table: entry m-1+k = root^(k L / 2m), for m = 1, 2, ..., 2^(tw_log-1)
+        std::vector<uint64_t> tw;
+        tw.reserve(2 * ((size_t)1 << pl->tw_log));
+        for (int b = 0; b < pl->tw_log; ++b) {
+            const uint64_t m = 1ull << b;
+            const uint64_t step = nt::powmod(root, pl->L / (2 * m), p);
+            uint64_t w = 1;
+            for (uint64_t k = 0; k < m; ++k) {
+                push_pair(tw, w, p, bits);
+                w = nt::mulmod(w, step, p);
+            }
+        }
+        int rc = upload_pairs(pl, tw, &pl->tw[d]);
+        if (rc) return rc;
+        // middle tables of the column passes
+        int logB = pl->logL;
+        for (int q = 0; q < pl->npass - 1; ++q) {
+            ntt::PassPlan &ps = pl->pass[q];
+            const int logR = ps.logR, logS = logB - logR;
+            const uint64_t R = 1ull << logR;
+            const uint64_t u = pl->L >> logB;  // middle twiddle omega^(u c rev(s))
+            std::vector<uint64_t> ma, mb;
+            ma.reserve(2 * (R << ps.logTA));
+            for (uint64_t s = 0; s < R; ++s) {
+                const uint64_t z = nt::powmod(root, (u * nt::bitrev((uint32_t)s, logR)) % pl->L, p);
+                uint64_t w = 1;
+                for (uint64_t c = 0; c < (1ull << ps.logTA); ++c) {
+                    push_pair(ma, w, p, bits);
+                    w = nt::mulmod(w, z, p);
+                }
+            }
+            rc = upload_pairs(pl, ma, &ps.ma[d]);
+            if (rc) return rc;
+            if (ps.has_mb) {
+                const uint64_t nhi = 1ull << (logS - ps.logTA);
+                mb.assign(2 * nhi * R, 0);
+                for (uint64_t s = 0; s < R; ++s) {
+                    const uint64_t zt = nt::powmod(root, ((u * nt::bitrev((uint32_t)s, logR)) << ps.logTA) % pl->L, p);
+                    uint64_t w = 1;
+                    for (uint64_t chi = 0; chi < nhi; ++chi) {
+                        mb[2 * (chi * R + s)] = w;
+                        mb[2 * (chi * R + s) + 1] = nt::shoup_quotient(w, p, bits);
+                        w = nt::mulmod(w, zt, p);
+                    }
+                }
+                rc = upload_pairs(pl, mb, &ps.mb[d]);
+                if (rc) return rc;
+            }
+            logB -= logR;
+        }
+    }
+    (void)logV;
+    return NTT_OK;
+}
+
+static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
+    pl->npass = n;
+    const int logV = pl->wbytes == 4 ? 2 : 1;
+    int logB = pl->logL;
+    for (int q = 0; q < kMaxPasses; ++q) pl->pass[q] = PassPlan();
+    for (int q = 0; q < n; ++q) {
+        PassPlan &ps = pl->pass[q];
+        ps.logR = logr[q];
+        ps.logS = q == n - 1 ? 0 : logB - logr[q];
+        if (q < n - 1) {
+            ps.logTV = max_logtv(ps.logS, pl->wbytes);
+            const int logT = ps.logTV + logV;
+            ps.logTA = std::min(ps.logS, std::max(logT, (ps.logS + 1) / 2));
+            ps.has_mb = ps.logTA < ps.logS;
+        }
+        logB -= logr[q];
+    }
+    return build_tables(pl);
+}
+
+// ---------------------------------------------------------------- launches
+
+static cudaError_t launch(const ntt_plan_s *pl, const LaunchSpec &s, int kind, int dir, cudaStream_t st) {
+    const int var = pl->variant == NTT_VARIANT_NTL ? 1 : 0;
+    return pl->wbytes == 4 ? launch_pass_u32(s, kind, dir, var, st) : launch_pass_u64(s, kind, dir, var, st);
+}
+
+int enqueue_transform(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stride, cudaStream_t st) {
+    return enqueue_steps(pl, dir, data, batch, stride, st, 0, pl->logL <= 2 ? 1 : pl->npass);
+}
+
+int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stride, cudaStream_t st, int first,
+                  int count) {
+    const int logV = pl->wbytes == 4 ? 2 : 1;
+    LaunchSpec s;
+    memset(&s, 0, sizeof(s));
+    s.data = data;
+    s.stride = stride;
+    s.batch = (uint32_t)batch;
+    s.logL = pl->logL;
+    s.p = pl->p;
+    s.tw = pl->tw[dir];
+    if (pl->logL <= 2) {
+        s.grid = (unsigned)((batch + 127) / 128);
+        cudaError_t e = launch(pl, s, 2, dir, st);
+        return e == cudaSuccess ? NTT_OK : cuda_fail(e, "launch tiny");
+    }
+    const int n = pl->npass;
+    for (int i = first; i < first + count && i < n; ++i) {
+        const int q = dir == 0 ? i : n - 1 - i;  // inverse runs the passes backwards
+        const PassPlan &ps = pl->pass[q];
+        s.logR = ps.logR;
+        s.logS = ps.logS;
+        s.flags = 0;
+        const bool last_exec = (i == n - 1);
+        if (last_exec) s.flags |= 1;  // F_NORMALIZE
+        const uint32_t R = 1u << ps.logR;
+        int kind;
+        if (q == n - 1) {  // row pass
+            kind = 1;
+            s.logTV = 0;
+            s.per_cta = (int)std::max<uint32_t>(1, 2048u / R);
+            s.nrows = (uint64_t)batch << (pl->logL - ps.logR);
+            const uint64_t rows_per_cta = (uint64_t)s.per_cta << logV;
+            s.grid = (unsigned)((s.nrows + rows_per_cta - 1) / rows_per_cta);
+            s.smem = (size_t)s.per_cta * R * 16;
+            s.ma = s.mb = nullptr;
+        } else {
+            kind = 0;
+            // Narrower tiles (down to 32-byte rows) when 128-byte rows would
+            // leave fewer than two CTAs per SM.
+            int logTV = ps.logTV;
+            while (logTV > 1 && ((uint64_t)batch << (pl->logL - ps.logR - logTV - logV)) < 2 * 152) --logTV;
+            s.logTV = logTV;
+            s.logTA = ps.logTA;
+            s.flags |= 2 | (ps.has_mb ? 4 : 0);  // F_MIDDLE, F_MB
+            s.ma = ps.ma[dir];
+            s.mb = ps.mb[dir];
+            const uint32_t tile_chunks = R << logTV;
+            const uint32_t tile_units = tile_chunks >> 3;
+            s.per_cta = (int)std::max<uint32_t>(1, 256u / std::max<uint32_t>(tile_units, 1));
+            while ((size_t)s.per_cta * tile_chunks * 16 > 64 * 1024 && s.per_cta > 1) s.per_cta >>= 1;
+            const uint64_t tiles = (uint64_t)batch << (pl->logL - ps.logR - logTV - logV);
+            s.grid = (unsigned)((tiles + s.per_cta - 1) / s.per_cta);
+            s.smem = (size_t)s.per_cta * tile_chunks * 16;
+            s.nrows = 0;
+        }
+        cudaError_t e = launch(pl, s, kind, dir, st);
+        if (e != cudaSuccess) return cuda_fail(e, "launch pass");
+    }
+    return NTT_OK;
+}
+
+}  // namespace ntt
+
+using namespace ntt;
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int ntt_version(void) { return 100; }
+
+const char *ntt_strerror(int code) {
+    switch (code) {
+        case NTT_OK: return "ok";
+        case NTT_ERR_MODULUS: return "modulus is not a prime below 2^62";
+        case NTT_ERR_LENGTH: return "length is not a power of two >= 2 dividing p-1";
+        case NTT_ERR_ROOT: return "omega is not a primitive L-th root of unity";
+        case NTT_ERR_ARG: return "invalid argument";
+        case NTT_ERR_CUDA: return "CUDA runtime error";
+        case NTT_ERR_NOMEM: return "out of memory";
+        case NTT_ERR_TIMEOUT: return "device-side wait timed out";
+        case NTT_ERR_ALIGN: return "pointer or stride not 16-byte aligned";
+        case NTT_ERR_RANGE: return "size beyond the supported maximum";
+        case NTT_ERR_REFUSED: return "request refused by admission control";
+        case NTT_ERR_CANCELLED: return "request cancelled";
+        case NTT_ERR_PENDING: return "request pending";
+        case NTT_ERR_FAILED: return "request failed";
+        default: return "unknown status";
+    }
+}
+
+const char *ntt_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+int ntt_is_prime(uint64_t n, int *is_prime) {
+    if (!is_prime) return NTT_ERR_ARG;
+    *is_prime = nt::is_prime(n) ? 1 : 0;
+    return NTT_OK;
+}
+
+int ntt_root_of_unity(uint64_t p, uint64_t L, uint64_t *omega) {
+    if (!omega) return NTT_ERR_ARG;
+    if (p < 3 || p >= (1ull << 62) || !nt::is_prime(p)) return NTT_ERR_MODULUS;
+    if (L < 1 || (L & (L - 1)) || (p - 1) % L) return NTT_ERR_LENGTH;
+    const uint64_t g = nt::smallest_qnr(p);
+    *omega = nt::powmod(g, (p - 1) / L, p);
+    return NTT_OK;
+}
+
+int ntt_find_prime(uint64_t lo, int k, uint64_t *q) {
+    if (!q || k < 1 || k > 62) return NTT_ERR_ARG;
+    const uint64_t step = 1ull << k;
+    uint64_t c = (lo / step) * step + 1;
+    while (c <= lo) c += step;
+    for (; c > lo; c += step) {
+        if (nt::is_prime(c)) {
+            *q = c;
+            return NTT_OK;
+        }
+    }
+    return NTT_ERR_RANGE;
+}
+
+int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L) {
+    if (!out) return NTT_ERR_ARG;
+    *out = nullptr;
+    if (p < 3 || p >= (1ull << 62) || !nt::is_prime(p)) return NTT_ERR_MODULUS;
+    if (L < 2 || (L & (L - 1))) return NTT_ERR_LENGTH;
+    if (L > (1ull << 26)) return NTT_ERR_RANGE;
+    if ((p - 1) % L) return NTT_ERR_LENGTH;
+    if (omega == 0 || omega >= p || nt::powmod(omega, L / 2, p) != p - 1) return NTT_ERR_ROOT;
+    ntt_plan_s *pl = new (std::nothrow) ntt_plan_s();
+    if (!pl) return NTT_ERR_NOMEM;
+    pl->p = p;
+    pl->omega = omega;
+    pl->omega_inv = nt::powmod(omega, p - 2, p);
+    pl->L = L;
+    pl->L_inv = nt::powmod(L % p, p - 2, p);
+    pl->logL = ilog2u(L);
+    pl->wbytes = p < (1ull << 30) ? 4 : 8;
+    cudaGetDevice(&pl->device);
+    int logr[kMaxPasses];
+    int n = default_split(pl->logL, pl->wbytes, logr);
+    int rc = apply_split(pl, n, logr);
+    if (rc) {
+        free_tables(pl);
+        delete pl;
+        return rc;
+    }
+    *out = pl;
+    return NTT_OK;
+}
+
+int ntt_plan_destroy(ntt_plan_t pl) {
+    if (!pl) return NTT_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_tables(pl);
+    if (pl->stage) cudaFree(pl->stage);
+    delete pl;
+    return NTT_OK;
+}
+
+int ntt_plan_set_variant(ntt_plan_t pl, int variant) {
+    if (!pl || (variant != NTT_VARIANT_LAZY && variant != NTT_VARIANT_NTL)) return NTT_ERR_ARG;
+    pl->variant = variant;
+    return NTT_OK;
+}
+
+int ntt_plan_get_info(ntt_plan_t pl, ntt_plan_info_t *info) {
+    if (!pl || !info) return NTT_ERR_ARG;
+    memset(info, 0, sizeof(*info));
+    info->p = pl->p;
+    info->omega = pl->omega;
+    info->omega_inv = pl->omega_inv;
+    info->L = pl->L;
+    info->L_inv = pl->L_inv;
+    info->log_L = pl->logL;
+    info->word_bytes = pl->wbytes;
+    info->variant = pl->variant;
+    info->n_passes = pl->npass;
+    for (int q = 0; q < pl->npass && q < 4; ++q) info->log_r[q] = pl->pass[q].logR;
+    info->table_bytes = pl->table_bytes;
+    return NTT_OK;
+}
+
+int ntt_plan_set_split(ntt_plan_t pl, int n_passes, const int *log_r) {
+    if (!pl || !log_r) return NTT_ERR_ARG;
+    if (!split_ok(pl->logL, pl->wbytes, n_passes, log_r)) return NTT_ERR_ARG;
+    cudaDeviceSynchronize();
+    return apply_split(pl, n_passes, log_r);
+}
+
+static int check_batch_args(ntt_plan_t pl, const void *d, size_t batch, size_t stride) {
+    if (!pl || !d || batch == 0) return NTT_ERR_ARG;
+    if (stride < pl->L) return NTT_ERR_ARG;
+    if (((uintptr_t)d & 15) || ((stride * pl->wbytes) & 15)) return NTT_ERR_ALIGN;
+    if (batch > (1ull << 31) / std::max<uint64_t>(1, pl->L / 8)) return NTT_ERR_RANGE;
+    return NTT_OK;
+}
+
+int ntt_forward_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_words, void *stream) {
+    int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc) return rc;
+    return enqueue_transform(pl, 0, d_data, batch, stride_words, (cudaStream_t)stream);
+}
+
+int ntt_inverse_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_words, void *stream) {
+    int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc) return rc;
+    return enqueue_transform(pl, 1, d_data, batch, stride_words, (cudaStream_t)stream);
+}
+
+int ntt_execute_step(ntt_plan_t pl, int inverse, int step, void *d_data, size_t batch, size_t stride_words,
+                     void *stream) {
+    int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc) return rc;
+    const int n = pl->logL <= 2 ? 1 : pl->npass;
+    if ((inverse != 0 && inverse != 1) || step < 0 || step >= n) return NTT_ERR_ARG;
+    return enqueue_steps(pl, inverse, d_data, batch, stride_words, (cudaStream_t)stream, step, 1);
+}
+
+int ntt_transform_host(ntt_plan_t pl, int inverse, void *h_data, size_t batch, size_t stride_words, void *stream) {
+    if (!pl || !h_data || batch == 0 || (inverse != 0 && inverse != 1)) return NTT_ERR_ARG;
+    if (stride_words < pl->L || ((stride_words * pl->wbytes) & 15)) return NTT_ERR_ALIGN;
+    std::lock_guard<std::mutex> lk(pl->mu);
+    const size_t bytes = batch * stride_words * pl->wbytes;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (pl->stage_bytes < bytes) {
+        if (pl->stage) {
+            cudaStreamSynchronize(st);
+            cudaFree(pl->stage);
+        }
+        pl->stage = nullptr;
+        pl->stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&pl->stage, bytes);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "cudaMalloc");
+        pl->stage_bytes = bytes;
+    }
+    cudaError_t e = cudaMemcpyAsync(pl->stage, h_data, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "H2D");
+    int rc = enqueue_transform(pl, inverse, pl->stage, batch, stride_words, st);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(h_data, pl->stage, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "D2H");
+    e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "sync");
+}
+
+}  // extern "C"

@@ -1,0 +1,23 @@
+// ntt_polymul.hpp -- internal entry points of the polynomial product, shared
+// with the serving loop.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "ntt_internal.hpp"
+
+namespace ntt {
+
+// Check (p, na, nb); on success *L_out = max(2, nextpow2(na + nb - 1)).
+int polymul_validate(uint64_t p, size_t na, size_t nb, uint64_t *L_out);
+
+// Cached plan for (current device, p, L) with the library's root of unity.
+int polymul_plan(uint64_t p, uint64_t L, ntt_plan_s **out);
+
+// Enqueue c = a * b on `st` using `buf` (2 L words of device scratch).
+int enqueue_polymul(ntt_plan_s *pl, const void *a, size_t na, const void *b, size_t nb, void *c, void *buf,
+                    cudaStream_t st);
+
+}  // namespace ntt

@@ -1,0 +1,421 @@
+// ntt_server.cu -- continuous-batching server for polynomial products mod p
+// (the application of Section 1 of Harvey, arXiv:1205.2926, under load).
+//
+// A scheduler thread owns the GPU work.  Submitted requests wait in a FIFO
+// queue; the scheduler admits them in order while their device memory fits
+// in the budget, groups the admitted ones by transform length L, and runs
+// each group as one batch on the next of several CUDA streams:
+//   zero the slab, copy operands in, forward transforms (2n vectors),
+//   pointwise product times L^-1, inverse transforms (n vectors), copy the
+//   na+nb-1 result words of each request straight to its host buffer.
+// Requests that arrive while batches are on the GPU are admitted as soon as
+// memory frees up, into new batches on other streams, so their work overlaps
+// with the running ones.  Plans and twiddle tables stay resident on the
+// device (one cached plan per (p, L)).  A batch is the same arithmetic as a
+// lone polymul_mod_p call, so each result is identical alone or in a mix.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "modarith.cuh"
+#include "ntt_internal.hpp"
+#include "ntt_polymul.hpp"
+
+namespace ntt {
+
+template <typename W>
+__global__ void k_pointwise_batch(W *__restrict__ A, const W *__restrict__ B, uint64_t n, W p, W J, W K, W Kq) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        W y = mont_mul(A[i], B[i], J, p);
+        A[i] = shoup_mul(y, K, Kq, p);
+    }
+}
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t id;
+    const void *a, *b;
+    void *c;
+    size_t na, nb;
+    uint64_t L;
+    Clock::time_point t_submit, t_done;
+    int status;  // NTT_ERR_PENDING while queued or running
+};
+
+struct Batch {
+    std::vector<uint64_t> ids;
+    ntt_plan_s *plan = nullptr;
+    void *slab = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t done = nullptr;
+    int stream = 0;
+    int status = NTT_OK;
+};
+
+}  // namespace ntt
+
+struct ntt_server_s {
+    ntt_server_config_t cfg;
+    int device = 0;
+    size_t wbytes = 4;
+    std::vector<cudaStream_t> streams;
+    int next_stream = 0;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, ntt::Request> reqs;
+    std::vector<ntt::Batch> inflight;
+    size_t inflight_bytes = 0;
+    uint64_t next_id = 1;
+    bool stop = false;
+    int fail_next = 0;
+    // statistics
+    std::vector<double> lat_us;
+    uint64_t n_done = 0, n_refused = 0, n_cancelled = 0, n_failed = 0, n_batches = 0;
+    double butterflies = 0;
+    ntt::Clock::time_point t_first, t_last;
+    bool any = false;
+    std::thread worker;
+};
+
+namespace ntt {
+
+static uint64_t bfly_count(uint64_t L) {
+    uint64_t l = 0;
+    while ((1ull << l) < L) ++l;
+    return 3 * l * (L / 2);  // two forward transforms and one inverse
+}
+
+// Launch one batch (scheduler thread, server lock held).
+template <typename W>
+static int launch_batch_t(ntt_server_s *sv, Batch &bt, const std::vector<Request *> &rs, cudaStream_t st) {
+    ntt_plan_s *pl = bt.plan;
+    const uint64_t L = pl->L, n = rs.size();
+    const size_t wb = sizeof(W);
+    cudaError_t e = cudaMallocAsync(&bt.slab, bt.bytes, st);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "server slab");
+    W *slab = (W *)bt.slab;
+    e = cudaMemsetAsync(slab, 0, bt.bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "server memset");
+    for (uint64_t i = 0; i < n; ++i) {
+        e = cudaMemcpyAsync(slab + i * L, rs[i]->a, rs[i]->na * wb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(slab + (n + i) * L, rs[i]->b, rs[i]->nb * wb, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "server H2D");
+    }
+    int rc = enqueue_transform(pl, 0, slab, 2 * n, L, st);
+    if (rc) return rc;
+    const int bits = pl->wbytes * 8;
+    uint64_t J = 1;
+    for (int i = 0; i < 7; ++i) J *= 2 - pl->p * J;
+    const uint64_t K = (uint64_t)(((unsigned __int128)pl->L_inv << bits) % pl->p);
+    const uint64_t Kq = nt::shoup_quotient(K, pl->p, bits);
+    const uint64_t total = n * L;
+    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 152 * 16);
+    k_pointwise_batch<W><<<grid, 256, 0, st>>>(slab, slab + total, total, (W)pl->p, (W)J, (W)K, (W)Kq);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "server pointwise");
+    rc = enqueue_transform(pl, 1, slab, n, L, st);
+    if (rc) return rc;
+    for (uint64_t i = 0; i < n; ++i) {
+        e = cudaMemcpyAsync(rs[i]->c, slab + i * L, (rs[i]->na + rs[i]->nb - 1) * wb, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "server D2H");
+    }
+    e = cudaFreeAsync(bt.slab, st);
+    bt.slab = nullptr;
+    if (e != cudaSuccess) return cuda_fail(e, "server free");
+    e = cudaEventRecord(bt.done, st);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "server event");
+}
+
+static void finish_request(ntt_server_s *sv, Request &r, int status) {
+    r.status = status;
+    r.t_done = Clock::now();
+    if (status == NTT_OK) {
+        sv->n_done++;
+        sv->lat_us.push_back(std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count());
+        sv->butterflies += (double)bfly_count(r.L);
+        sv->t_last = r.t_done;
+    } else if (status == NTT_ERR_FAILED) {
+        sv->n_failed++;
+    }
+}
+
+static void scheduler(ntt_server_s *sv) {
+    cudaSetDevice(sv->device);
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (true) {
+        // 1. completions
+        bool progressed = false;
+        for (size_t i = 0; i < sv->inflight.size();) {
+            Batch &bt = sv->inflight[i];
+            cudaError_t q = cudaEventQuery(bt.done);
+            if (q == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
+            const int st = (q == cudaSuccess && bt.status == NTT_OK) ? NTT_OK : NTT_ERR_FAILED;
+            if (q != cudaSuccess && q != cudaErrorNotReady) cudaGetLastError();
+            for (uint64_t id : bt.ids) finish_request(sv, sv->reqs[id], st);
+            sv->inflight_bytes -= bt.bytes;
+            cudaEventDestroy(bt.done);
+            sv->inflight.erase(sv->inflight.begin() + i);
+            progressed = true;
+        }
+        if (progressed) sv->done_cv.notify_all();
+        if (sv->stop && sv->queue.empty() && sv->inflight.empty()) break;
+        // 2. admission in FIFO order while memory allows
+        std::map<uint64_t, std::vector<uint64_t>> by_len;
+        size_t admitted_bytes = 0;
+        while (!sv->queue.empty()) {
+            Request &r = sv->reqs[sv->queue.front()];
+            const size_t need = 2 * r.L * sv->wbytes;
+            if (sv->inflight_bytes + admitted_bytes + need > sv->cfg.mem_budget_bytes) break;
+            auto &v = by_len[r.L];
+            if ((int)v.size() >= sv->cfg.max_batch) break;
+            v.push_back(r.id);
+            admitted_bytes += need;
+            sv->queue.pop_front();
+        }
+        // 3. launch one batch per length class
+        for (auto &kv : by_len) {
+            Batch bt;
+            bt.ids = kv.second;
+            bt.bytes = 2 * kv.first * sv->wbytes * bt.ids.size();
+            bt.stream = sv->next_stream;
+            sv->next_stream = (sv->next_stream + 1) % (int)sv->streams.size();
+            cudaEventCreateWithFlags(&bt.done, cudaEventDisableTiming);
+            std::vector<Request *> rs;
+            for (uint64_t id : bt.ids) rs.push_back(&sv->reqs[id]);
+            int rc = polymul_plan(sv->cfg.p, kv.first, &bt.plan);
+            if (rc == NTT_OK && sv->fail_next > 0) {
+                sv->fail_next--;
+                rc = NTT_ERR_FAILED;  // host-side failure injection
+            }
+            if (rc == NTT_OK) {
+                cudaStream_t st = sv->streams[bt.stream];
+                rc = sv->wbytes == 4 ? launch_batch_t<uint32_t>(sv, bt, rs, st) : launch_batch_t<uint64_t>(sv, bt, rs, st);
+            }
+            if (rc != NTT_OK) {
+                // this batch fails; the others are unaffected
+                if (bt.slab) cudaFreeAsync(bt.slab, sv->streams[bt.stream]);
+                cudaStreamSynchronize(sv->streams[bt.stream]);
+                cudaGetLastError();
+                for (Request *r : rs) finish_request(sv, *r, NTT_ERR_FAILED);
+                cudaEventDestroy(bt.done);
+                sv->done_cv.notify_all();
+                continue;
+            }
+            sv->n_batches++;
+            sv->inflight_bytes += bt.bytes;
+            sv->inflight.push_back(bt);
+        }
+        // 4. wait for work: short sleeps while batches run, block when idle
+        if (!sv->inflight.empty()) {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        } else if (sv->queue.empty() && !sv->stop) {
+            sv->cv.wait(lk, [sv] { return sv->stop || !sv->queue.empty(); });
+        } else if (!sv->queue.empty() && by_len.empty()) {
+            // head of the queue cannot be admitted yet and nothing runs: it
+            // can never fit (guarded at submit), so this is unreachable; yield
+            lk.unlock();
+            std::this_thread::yield();
+            lk.lock();
+        }
+    }
+}
+
+}  // namespace ntt
+
+using namespace ntt;
+
+extern "C" {
+
+int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out) {
+    if (!cfg || !out) return NTT_ERR_ARG;
+    *out = nullptr;
+    if (cfg->p < 3 || cfg->p >= (1ull << 62) || !nt::is_prime(cfg->p)) return NTT_ERR_MODULUS;
+    if (cfg->max_coeffs == 0 || cfg->mem_budget_bytes == 0 || cfg->n_streams < 1 || cfg->n_streams > 64 ||
+        cfg->max_batch < 1)
+        return NTT_ERR_ARG;
+    uint64_t L = 0;
+    int rc = polymul_validate(cfg->p, cfg->max_coeffs, cfg->max_coeffs, &L);
+    if (rc) return rc;
+    ntt_server_s *sv = new (std::nothrow) ntt_server_s();
+    if (!sv) return NTT_ERR_NOMEM;
+    sv->cfg = *cfg;
+    sv->wbytes = cfg->p < (1ull << 30) ? 4 : 8;
+    cudaGetDevice(&sv->device);
+    for (int i = 0; i < cfg->n_streams; ++i) {
+        cudaStream_t s;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (cudaStream_t t : sv->streams) cudaStreamDestroy(t);
+            delete sv;
+            return cuda_fail(e, "server stream");
+        }
+        sv->streams.push_back(s);
+    }
+    sv->worker = std::thread(scheduler, sv);
+    *out = sv;
+    return NTT_OK;
+}
+
+int ntt_server_submit(ntt_server_t sv, const void *h_a, size_t na, const void *h_b, size_t nb, void *h_c,
+                      uint64_t *req_id) {
+    if (!sv || !h_a || !h_b || !h_c || !req_id) return NTT_ERR_ARG;
+    uint64_t L = 0;
+    int rc = polymul_validate(sv->cfg.p, na, nb, &L);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    Request r;
+    r.id = sv->next_id++;
+    r.a = h_a;
+    r.b = h_b;
+    r.c = h_c;
+    r.na = na;
+    r.nb = nb;
+    r.L = L;
+    r.t_submit = Clock::now();
+    if (!sv->any) {
+        sv->any = true;
+        sv->t_first = r.t_submit;
+    }
+    *req_id = r.id;
+    if (rc != NTT_OK || na > sv->cfg.max_coeffs || nb > sv->cfg.max_coeffs ||
+        2 * L * sv->wbytes > sv->cfg.mem_budget_bytes) {
+        r.status = NTT_ERR_REFUSED;
+        sv->n_refused++;
+        sv->reqs[r.id] = r;
+        return NTT_ERR_REFUSED;
+    }
+    r.status = NTT_ERR_PENDING;
+    sv->reqs[r.id] = r;
+    sv->queue.push_back(r.id);
+    sv->cv.notify_one();
+    return NTT_OK;
+}
+
+int ntt_server_poll(ntt_server_t sv, uint64_t id, int *status) {
+    if (!sv || !status) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return NTT_ERR_ARG;
+    *status = it->second.status;
+    return NTT_OK;
+}
+
+int ntt_server_wait(ntt_server_t sv, uint64_t id, int timeout_ms, int *status) {
+    if (!sv || !status) return NTT_ERR_ARG;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return NTT_ERR_ARG;
+    auto ready = [&] { return sv->reqs[id].status != NTT_ERR_PENDING; };
+    if (timeout_ms < 0)
+        sv->done_cv.wait(lk, ready);
+    else
+        sv->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    *status = sv->reqs[id].status;
+    return NTT_OK;
+}
+
+int ntt_server_cancel(ntt_server_t sv, uint64_t id) {
+    if (!sv) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end()) return NTT_ERR_ARG;
+    auto q = std::find(sv->queue.begin(), sv->queue.end(), id);
+    if (q == sv->queue.end()) return NTT_ERR_PENDING;  // already admitted or finished
+    sv->queue.erase(q);
+    it->second.status = NTT_ERR_CANCELLED;
+    sv->n_cancelled++;
+    sv->done_cv.notify_all();
+    return NTT_OK;
+}
+
+int ntt_server_drain(ntt_server_t sv, int timeout_ms) {
+    if (!sv) return NTT_ERR_ARG;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto idle = [sv] { return sv->queue.empty() && sv->inflight.empty(); };
+    if (timeout_ms < 0) {
+        sv->done_cv.wait(lk, idle);
+        return NTT_OK;
+    }
+    return sv->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle) ? NTT_OK : NTT_ERR_PENDING;
+}
+
+int ntt_server_stats(ntt_server_t sv, ntt_server_stats_t *out) {
+    if (!sv || !out) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    memset(out, 0, sizeof(*out));
+    out->completed = sv->n_done;
+    out->refused = sv->n_refused;
+    out->cancelled = sv->n_cancelled;
+    out->failed = sv->n_failed;
+    out->batches = sv->n_batches;
+    out->butterflies = sv->butterflies;
+    std::vector<double> v = sv->lat_us;
+    if (!v.empty()) {
+        std::sort(v.begin(), v.end());
+        auto pct = [&](double q) { return v[std::min(v.size() - 1, (size_t)(q * (v.size() - 1) + 0.5))]; };
+        out->p50_us = pct(0.50);
+        out->p99_us = pct(0.99);
+        out->max_us = v.back();
+        double s = 0;
+        for (double x : v) s += x;
+        out->mean_us = s / v.size();
+    }
+    if (sv->any && sv->n_done) out->wall_s = std::chrono::duration<double>(sv->t_last - sv->t_first).count();
+    return NTT_OK;
+}
+
+int ntt_server_reset_stats(ntt_server_t sv) {
+    if (!sv) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->lat_us.clear();
+    sv->n_done = sv->n_refused = sv->n_cancelled = sv->n_failed = sv->n_batches = 0;
+    sv->butterflies = 0;
+    sv->any = false;
+    for (auto it = sv->reqs.begin(); it != sv->reqs.end();) {
+        if (it->second.status != NTT_ERR_PENDING)
+            it = sv->reqs.erase(it);
+        else
+            ++it;
+    }
+    return NTT_OK;
+}
+
+int ntt_server_inject_failures(ntt_server_t sv, int n_batches) {
+    if (!sv || n_batches < 0) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->fail_next = n_batches;
+    return NTT_OK;
+}
+
+int ntt_server_destroy(ntt_server_t sv) {
+    if (!sv) return NTT_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stop = true;
+        sv->cv.notify_all();
+    }
+    sv->worker.join();
+    for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+    delete sv;
+    return NTT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+// ntt_uneven.cu -- many transforms of different lengths, primes and
+// directions in ONE persistent kernel launch.
+//
+// Host side: descriptors are grouped by (plan, direction).  A group whose
+// plan runs in a single pass (L <= 2^12) becomes one "class task" whose rows
+// are the transforms themselves (row addresses gathered in a device table),
+// so one CTA packs many short transforms that share twiddles.  Every
+// transform of a multi-pass plan becomes its own task with one stage per
+// pass.  Work items (one CTA's worth of one stage of one task) are listed in
+// dependency order: first-stage items of multi-pass tasks, then the
+// single-pass items, then later stages.
+//
+// Device side: each CTA of the persistent grid takes the next item from an
+// atomic counter.  An item of stage s > 0 waits until every item of stage
+// s-1 of its task has finished (a per-(task, stage) completion counter).  It
+// only ever waits for items with a smaller index, which were taken by CTAs
+// already running, so the waits cannot deadlock whatever the residency.
+// Every wait is bounded by a clock budget; on expiry the CTA records
+// NTT_ERR_TIMEOUT in a status word, raises an abort flag that makes every
+// other CTA stop at its next check, and returns.  Inputs of later stages are
+// read with L1-bypassing loads because other CTAs of the same launch wrote
+// them.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "ntt_internal.hpp"
+#include "ntt_kernels.cuh"
+
+namespace ntt {
+
+struct UStage {
+    const uint32_t *ma, *mb;
+    uint32_t units;  // CTAs-worth of work (items) in this stage
+    int8_t logR, logS, logTV, logTA, row;
+    uint8_t flags;
+    uint16_t per_cta;
+};
+
+struct UTask {
+    uint32_t *data;            // multi-pass task: the transform
+    uint32_t *const *rowptrs;  // class task: one row address per transform
+    const uint32_t *tw;
+    uint64_t nrows;            // class task: number of transforms
+    uint32_t p;
+    uint32_t done_base;        // first completion counter of this task
+    int8_t logL, nstages, dir;
+    UStage st[kMaxPasses];
+};
+
+struct UItem {
+    uint32_t task;
+    uint32_t stage;
+    uint32_t cta;  // CTA index within the stage
+};
+
+struct UCtl {
+    unsigned int next;       // next item to take
+    int status;              // NTT_OK or NTT_ERR_TIMEOUT
+    int abort;               // set on timeout: every CTA stops
+    unsigned int pad;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile const int *)p; }
+
+template <int DIR, bool ROW>
+__device__ __forceinline__ void run_item(const UTask &t, const UStage &sg, uint32_t cta, uint4 *sm) {
+    PassArgs<uint32_t> a;
+    a.data = t.data;
+    a.stride = 1u << t.logL;
+    a.batch = 1;
+    a.logL = t.logL;
+    a.logR = sg.logR;
+    a.logS = sg.logS;
+    a.per_cta = sg.per_cta;
+    a.logTV = sg.logTV;
+    a.logTA = sg.logTA;
+    a.flags = sg.flags;
+    a.tw = t.tw;
+    a.ma = sg.ma;
+    a.mb = sg.mb;
+    a.p = t.p;
+    a.rowptrs = t.rowptrs;
+    a.nrows = t.rowptrs ? t.nrows : (1ull << (t.logL - sg.logR));
+    pass_cta<uint32_t, DIR, VAR_LAZY, ROW, true>(a, cta, sm);
+}
+
+__global__ void __launch_bounds__(kThreads) k_uneven(const UTask *__restrict__ tasks, const UItem *__restrict__ items,
+                                                      uint32_t n_items, unsigned int *done, UCtl *ctl,
+                                                      long long wait_budget, int stall_stage) {
+    extern __shared__ uint4 sm[];
+    __shared__ unsigned int s_item;
+    __shared__ int s_skip;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_item = ld_volatile(&ctl->abort) ? n_items : atomicAdd(&ctl->next, 1u);
+            s_skip = 0;
+        }
+        __syncthreads();
+        const unsigned int it = s_item;
+        if (it >= n_items) break;
+        const UItem item = items[it];
+        const UTask &t = tasks[item.task];
+        if (item.stage > 0 && threadIdx.x == 0) {
+            const UStage &prev = t.st[item.stage - 1];
+            // A stall injected for testing asks for one completion more than
+            // will ever happen, so that the bounded wait must give up.
+            const unsigned int need = prev.units + (stall_stage == (int)item.stage ? 1u : 0u);
+            const unsigned int *cnt = done + t.done_base + item.stage - 1;
+            const long long t0 = clock64();
+            while (ld_acquire(cnt) < need) {
+                if (ld_volatile(&ctl->abort)) {
+                    s_skip = 1;
+                    break;
+                }
+                if (clock64() - t0 > wait_budget) {
+                    atomicExch(&ctl->status, NTT_ERR_TIMEOUT);
+                    atomicExch(&ctl->abort, 1);
+                    s_skip = 1;
+                    break;
+                }
+                __nanosleep(256);
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        if (s_skip) break;
+        const UStage &sg = t.st[item.stage];
+        if (t.dir == DIR_FWD) {
+            if (sg.row)
+                run_item<DIR_FWD, true>(t, sg, item.cta, sm);
+            else
+                run_item<DIR_FWD, false>(t, sg, item.cta, sm);
+        } else {
+            if (sg.row)
+                run_item<DIR_INV, true>(t, sg, item.cta, sm);
+            else
+                run_item<DIR_INV, false>(t, sg, item.cta, sm);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(done + t.done_base + item.stage, 1u);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- host side
+
+struct Prepared {
+    std::vector<ntt_desc_t> key;
+    UTask *d_tasks = nullptr;
+    UItem *d_items = nullptr;
+    uint32_t **d_rowptrs = nullptr;
+    unsigned int *d_done = nullptr;
+    UCtl *d_ctl = nullptr;
+    uint32_t n_items = 0, n_done = 0;
+    size_t smem = 0;
+    unsigned grid = 0;
+    int device = -1;
+    void release() {
+        cudaFree(d_tasks);
+        cudaFree(d_items);
+        cudaFree(d_rowptrs);
+        cudaFree(d_done);
+        cudaFree(d_ctl);
+        d_tasks = nullptr;
+        d_items = nullptr;
+        d_rowptrs = nullptr;
+        d_done = nullptr;
+        d_ctl = nullptr;
+    }
+};
+
+static std::mutex g_mu;
+static std::map<int, Prepared> g_prep;  // last prepared batch per device
+static long long g_wait_budget = 2000000000LL;  // clock cycles (about 1 s)
+static int g_stall_stage = -1;
+
+static bool same_key(const std::vector<ntt_desc_t> &k, const ntt_desc_t *d, size_t n) {
+    if (k.size() != n) return false;
+    return n == 0 || memcmp(k.data(), d, n * sizeof(ntt_desc_t)) == 0;
+}
+
+// Stage geometry of pass q of a plan, executed in direction dir as step i.
+static UStage make_stage(const ntt_plan_s *pl, int dir, int i, uint32_t nrows_class, size_t *smem) {
+    const int n = pl->npass;
+    const int q = dir == 0 ? i : n - 1 - i;
+    const PassPlan &ps = pl->pass[q];
+    UStage sg;
+    memset(&sg, 0, sizeof(sg));
+    sg.logR = (int8_t)ps.logR;
+    sg.logS = (int8_t)ps.logS;
+    sg.flags = (i == n - 1) ? F_NORMALIZE : 0;
+    const uint32_t R = 1u << ps.logR;
+    if (q == n - 1) {
+        sg.row = 1;
+        sg.logTV = 0;
+        sg.per_cta = (uint16_t)std::max<uint32_t>(1, 2048u / R);
+        const uint64_t nrows = nrows_class ? nrows_class : (1ull << (pl->logL - ps.logR));
+        const uint64_t per = (uint64_t)sg.per_cta * 4;
+        sg.units = (uint32_t)((nrows + per - 1) / per);
+        *smem = std::max(*smem, (size_t)sg.per_cta * R * 16);
+    } else {
+        sg.row = 0;
+        sg.logTV = (int8_t)ps.logTV;
+        sg.logTA = (int8_t)ps.logTA;
+        sg.flags |= F_MIDDLE | (ps.has_mb ? F_MB : 0);
+        sg.ma = (const uint32_t *)ps.ma[dir];
+        sg.mb = (const uint32_t *)ps.mb[dir];
+        const uint32_t tile_chunks = R << ps.logTV;
+        uint32_t per = std::max<uint32_t>(1, 256u / std::max<uint32_t>(tile_chunks >> 3, 1));
+        while ((size_t)per * tile_chunks * 16 > 64 * 1024 && per > 1) per >>= 1;
+        sg.per_cta = (uint16_t)per;
+        const uint64_t tiles = 1ull << (pl->logL - ps.logR - ps.logTV - 2);
+        sg.units = (uint32_t)((tiles + per - 1) / per);
+        *smem = std::max(*smem, (size_t)per * tile_chunks * 16);
+    }
+    return sg;
+}
+
+static int prepare(const ntt_desc_t *descs, size_t n, Prepared &pr) {
+    pr.release();
+    pr.key.assign(descs, descs + n);
+    cudaGetDevice(&pr.device);
+    // group by (plan, direction), preserving first appearance
+    std::map<std::pair<ntt_plan_s *, int>, std::vector<size_t>> groups;
+    std::vector<std::pair<ntt_plan_s *, int>> order;
+    for (size_t i = 0; i < n; ++i) {
+        ntt_plan_s *pl = descs[i].plan;
+        if (!pl || !descs[i].d_data || (descs[i].inverse != 0 && descs[i].inverse != 1)) return NTT_ERR_ARG;
+        if (pl->wbytes != 4 || pl->variant != NTT_VARIANT_LAZY || pl->logL > 22 || pl->logL < 3) return NTT_ERR_RANGE;
+        if ((uintptr_t)descs[i].d_data & 15) return NTT_ERR_ALIGN;
+        auto k = std::make_pair(pl, descs[i].inverse);
+        if (!groups.count(k)) order.push_back(k);
+        groups[k].push_back(i);
+    }
+    std::vector<UTask> tasks;
+    std::vector<uint32_t *> rowptrs;
+    std::vector<size_t> rowptr_off;  // per class task: offset into rowptrs
+    std::vector<int> is_class;
+    size_t smem = 0;
+    uint32_t done = 0;
+    // multi-pass tasks first (longest first), then class tasks
+    std::stable_sort(order.begin(), order.end(), [](const std::pair<ntt_plan_s *, int> &x,
+                                                    const std::pair<ntt_plan_s *, int> &y) {
+        return x.first->logL > y.first->logL;
+    });
+    for (auto &k : order) {
+        ntt_plan_s *pl = k.first;
+        const int dir = k.second;
+        const auto &idx = groups[k];
+        if (pl->npass == 1) {
+            UTask t;
+            memset(&t, 0, sizeof(t));
+            t.tw = (const uint32_t *)pl->tw[dir];
+            t.p = (uint32_t)pl->p;
+            t.logL = (int8_t)pl->logL;
+            t.nstages = 1;
+            t.dir = (int8_t)dir;
+            t.nrows = idx.size();
+            t.done_base = done;
+            done += 1;
+            t.st[0] = make_stage(pl, dir, 0, (uint32_t)idx.size(), &smem);
+            rowptr_off.push_back(rowptrs.size());
+            for (size_t i : idx) rowptrs.push_back((uint32_t *)descs[i].d_data);
+            tasks.push_back(t);
+            is_class.push_back(1);
+        } else {
+            for (size_t i : idx) {
+                UTask t;
+                memset(&t, 0, sizeof(t));
+                t.data = (uint32_t *)descs[i].d_data;
+                t.tw = (const uint32_t *)pl->tw[dir];
+                t.p = (uint32_t)pl->p;
+                t.logL = (int8_t)pl->logL;
+                t.nstages = (int8_t)pl->npass;
+                t.dir = (int8_t)dir;
+                t.done_base = done;
+                done += pl->npass;
+                for (int s = 0; s < pl->npass; ++s) t.st[s] = make_stage(pl, dir, s, 0, &smem);
+                rowptr_off.push_back(0);
+                tasks.push_back(t);
+                is_class.push_back(0);
+            }
+        }
+    }
+    // items: stage 0 of multi-pass tasks, class tasks, then later stages
+    std::vector<UItem> items;
+    for (size_t ti = 0; ti < tasks.size(); ++ti)
+        if (!is_class[ti])
+            for (uint32_t c = 0; c < tasks[ti].st[0].units; ++c) items.push_back({(uint32_t)ti, 0, c});
+    for (size_t ti = 0; ti < tasks.size(); ++ti)
+        if (is_class[ti])
+            for (uint32_t c = 0; c < tasks[ti].st[0].units; ++c) items.push_back({(uint32_t)ti, 0, c});
+    for (int s = 1; s < kMaxPasses; ++s)
+        for (size_t ti = 0; ti < tasks.size(); ++ti)
+            if (!is_class[ti] && s < tasks[ti].nstages)
+                for (uint32_t c = 0; c < tasks[ti].st[s].units; ++c) items.push_back({(uint32_t)ti, (uint32_t)s, c});
+    // device copies
+    cudaError_t e;
+    if (!rowptrs.empty()) {
+        e = cudaMalloc(&pr.d_rowptrs, rowptrs.size() * sizeof(uint32_t *));
+        if (e != cudaSuccess) return NTT_ERR_NOMEM;
+        e = cudaMemcpy(pr.d_rowptrs, rowptrs.data(), rowptrs.size() * sizeof(uint32_t *), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "uneven rowptrs");
+        for (size_t ti = 0; ti < tasks.size(); ++ti)
+            if (is_class[ti]) tasks[ti].rowptrs = pr.d_rowptrs + rowptr_off[ti];
+    }
+    e = cudaMalloc(&pr.d_tasks, std::max<size_t>(1, tasks.size()) * sizeof(UTask));
+    if (e != cudaSuccess) return NTT_ERR_NOMEM;
+    e = cudaMalloc(&pr.d_items, std::max<size_t>(1, items.size()) * sizeof(UItem));
+    if (e != cudaSuccess) return NTT_ERR_NOMEM;
+    e = cudaMalloc(&pr.d_done, std::max<uint32_t>(1, done) * sizeof(unsigned int));
+    if (e != cudaSuccess) return NTT_ERR_NOMEM;
+    e = cudaMalloc(&pr.d_ctl, sizeof(UCtl));
+    if (e != cudaSuccess) return NTT_ERR_NOMEM;
+    if (!tasks.empty()) {
+        e = cudaMemcpy(pr.d_tasks, tasks.data(), tasks.size() * sizeof(UTask), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "uneven tasks");
+    }
+    if (!items.empty()) {
+        e = cudaMemcpy(pr.d_items, items.data(), items.size() * sizeof(UItem), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "uneven items");
+    }
+    pr.n_items = (uint32_t)items.size();
+    pr.n_done = done;
+    pr.smem = std::max<size_t>(smem, 16);
+    // persistent grid: as many CTAs as fit on the device at once
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pr.device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pr.device);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_uneven);
+    if (e != cudaSuccess) return cuda_fail(e, "uneven attr");
+    if (pr.smem + fa.sharedSizeBytes > (size_t)optin) return NTT_ERR_RANGE;
+    e = cudaFuncSetAttribute(k_uneven, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pr.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "uneven attr");
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uneven, kThreads, pr.smem);
+    if (e != cudaSuccess) return cuda_fail(e, "uneven occupancy");
+    pr.grid = (unsigned)std::max<long long>(1, std::min<long long>((long long)sms * std::max(per_sm, 1), pr.n_items));
+    return NTT_OK;
+}
+
+}  // namespace ntt
+
+using namespace ntt;
+
+extern "C" {
+
+int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream) {
+    if (!descs || n == 0) return NTT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    Prepared &pr = g_prep[dev];
+    if (!same_key(pr.key, descs, n) || pr.device != dev || !pr.d_ctl) {
+        cudaDeviceSynchronize();  // the previous batch's tables may still be in use
+        int rc = prepare(descs, n, pr);
+        if (rc) {
+            pr.release();
+            pr.key.clear();
+            return rc;
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(pr.d_done, 0, std::max<uint32_t>(1, pr.n_done) * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr.d_ctl, 0, sizeof(UCtl), st);
+    if (e != cudaSuccess) return cuda_fail(e, "uneven memset");
+    k_uneven<<<pr.grid, kThreads, pr.smem, st>>>(pr.d_tasks, pr.d_items, pr.n_items, pr.d_done, pr.d_ctl,
+                                                  g_wait_budget, g_stall_stage);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "k_uneven");
+}
+
+int ntt_uneven_status(int *status) {
+    if (!status) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto it = g_prep.find(dev);
+    if (it == g_prep.end() || !it->second.d_ctl) {
+        *status = NTT_OK;
+        return NTT_OK;
+    }
+    UCtl c;
+    cudaError_t e = cudaMemcpy(&c, it->second.d_ctl, sizeof(UCtl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "uneven status");
+    *status = c.status;
+    return NTT_OK;
+}
+
+int ntt_uneven_set_wait_budget(long long cycles, int stall_stage) {
+    if (cycles <= 0) return NTT_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_wait_budget = cycles;
+    g_stall_stage = stall_stage;
+    return NTT_OK;
+}
+
+}  // extern "C"

@@ -181,3 +181,17 @@ ALL_PINS = [
     pin_convolution_theorem,
     pin_linearity,
 ]
+
+
+def pin_dft_at(o):
+    """One-position evaluation agrees with Horner evaluation at omega^rev(k)."""
+    for p in (998244353, 2305843009448574977):
+        for l in (1, 5, 9):
+            L = 1 << l
+            w = primitive_root_of_order(p, L)
+            a = uniform_residues(7000 + l, L, p)
+            for k in (0, 1, L // 2, L - 1):
+                assert o.dft_at(p, w, a, k) == horner_eval(a, pow(w, bitrev(k, l), p), p)
+
+
+ALL_PINS.append(pin_dft_at)

@@ -1,0 +1,237 @@
+"""Parity of the CUDA transforms with the CPU oracle, bit-exact after the final
+reduction (Section 3), through the C ABI.  Every input is seeded.
+
+Covered: every length 2^1 .. 2^16 (single and multi-pass schedules) with a
+ragged batch and padded stride; the 32-bit and 64-bit word paths; the lazy
+(Algorithms 3/4) and NTL-style (Algorithm 2) variants; forward and inverse
+(Section 4); redundant inputs in [0,2p) / [0,4p); every allowed pass split at
+selected lengths; the full-size workloads (64 x 2^16, 2^20, 2^22 at 32 bits;
+16 x 2^20 and 2^24 at 64 bits) compared in full; argument errors."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1205_2926_gb300 as ntt
+from paper_1205_2926_gb300.inputs import P_NTT30, P_NTT62, P_UNEVEN, batch_inputs, uniform_residues, word_dtype
+from tests.gpu_util import from_dev, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+O = None
+
+
+def orc():
+    global O
+    if O is None:
+        O = oracle.get()
+    return O
+
+
+def run(plan, a_np, inverse, stride=None, variant=0, torch=None):
+    """Transform rows of a_np (batch, L) on the GPU; returns (batch, L) numpy."""
+    batch, L = a_np.shape
+    stride = stride or L
+    buf = np.zeros((batch, stride), dtype=a_np.dtype)
+    buf[:, :L] = a_np
+    if stride > L:
+        buf[:, L:] = np.iinfo(a_np.dtype).max  # padding must stay untouched
+    d = to_dev(buf, torch)
+    plan.set_variant(variant)
+    if inverse:
+        ntt.ntt_inverse_batch(plan, d, batch, stride)
+    else:
+        ntt.ntt_forward_batch(plan, d, batch, stride)
+    torch.cuda.synchronize()
+    out = from_dev(d, a_np.dtype).reshape(batch, stride)
+    if stride > L:
+        assert np.all(out[:, L:] == np.iinfo(a_np.dtype).max), "wrote outside the transform"
+    return out[:, :L]
+
+
+def pad_stride(L, wbytes, extra):
+    per16 = 16 // wbytes
+    return ((L + extra + per16 - 1) // per16) * per16
+
+
+@pytest.mark.parametrize("p", [P_NTT30, P_UNEVEN[0], P_NTT62])
+@pytest.mark.parametrize("logL", list(range(1, 17)))
+@pytest.mark.parametrize("variant", [0, 1])
+def test_forward_inverse_all_lengths(p, logL, variant):
+    torch = require_gpu()
+    L = 1 << logL
+    if (p - 1) % L:
+        pytest.skip("L does not divide p-1")
+    o = orc()
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    batch = 3
+    a = batch_inputs(100 + logL, batch, L, p)
+    stride = pad_stride(L, plan.word_bytes, 5)
+    got = run(plan, a, False, stride, variant, torch)
+    want = o.ntt_ref(p, w, a.astype(np.uint64))
+    assert np.array_equal(got.astype(np.uint64), want), f"forward p={p} L={L} variant={variant}"
+    y = batch_inputs(200 + logL, batch, L, p)
+    got = run(plan, y, True, stride, variant, torch)
+    want = o.intt_ref(p, w, y.astype(np.uint64))
+    assert np.array_equal(got.astype(np.uint64), want), f"inverse p={p} L={L} variant={variant}"
+    plan.destroy()
+
+
+@pytest.mark.parametrize("p", [P_NTT30, P_NTT62])
+@pytest.mark.parametrize("logL", [3, 9, 13, 16])
+def test_redundant_inputs(p, logL):
+    """Algorithm 3 accepts [0,2p) and Algorithm 4 accepts [0,4p) on input."""
+    torch = require_gpu()
+    L = 1 << logL
+    o = orc()
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    dt = word_dtype(p)
+    a = uniform_residues(300 + logL, 2 * L, 2 * p).astype(dt).reshape(2, L)
+    got = run(plan, a, False, None, 0, torch)
+    assert np.array_equal(got.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64) % np.uint64(p)))
+    y = uniform_residues(400 + logL, 2 * L, 4 * p).astype(dt).reshape(2, L)
+    got = run(plan, y, True, None, 0, torch)
+    assert np.array_equal(got.astype(np.uint64), o.intt_ref(p, w, y.astype(np.uint64) % np.uint64(p)))
+    plan.destroy()
+
+
+SPLITS = {
+    11: [[11], [3, 8], [6, 5], [3, 3, 5]],
+    14: [[7, 7], [3, 11], [9, 5], [4, 4, 6], [3, 3, 3, 5], [10, 4]],
+    17: [[5, 12], [9, 8], [10, 7], [4, 5, 8], [6, 6, 5]],
+}
+
+
+@pytest.mark.parametrize("p", [P_NTT30, P_NTT62])
+@pytest.mark.parametrize("logL,split", [(k, s) for k, v in SPLITS.items() for s in v])
+@pytest.mark.parametrize("variant", [0, 1])
+def test_every_split(p, logL, split, variant):
+    torch = require_gpu()
+    L = 1 << logL
+    o = orc()
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    min_after = 5 if plan.word_bytes == 4 else 4  # a column pass needs >= 128 bytes per tile row
+    valid = all(logL - sum(split[:i + 1]) >= min_after for i in range(len(split) - 1))
+    if not valid:
+        with pytest.raises(ntt.NTTError) as e:
+            plan.set_split(split)
+        assert e.value.code == -4
+        return
+    plan.set_split(split)
+    assert list(plan.info().log_r)[:len(split)] == split
+    a = batch_inputs(500 + logL, 2, L, p)
+    got = run(plan, a, False, None, variant, torch)
+    assert np.array_equal(got.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64)))
+    got = run(plan, a, True, None, variant, torch)
+    assert np.array_equal(got.astype(np.uint64), o.intt_ref(p, w, a.astype(np.uint64)))
+    plan.destroy()
+
+
+FULL = [
+    (P_NTT30, 16, 64),
+    (P_NTT30, 20, 1),
+    (P_NTT30, 22, 1),
+    (P_NTT62, 20, 16),
+    (P_NTT62, 24, 1),
+]
+
+
+@pytest.mark.parametrize("p,logL,batch", FULL)
+@pytest.mark.parametrize("variant", [0, 1])
+def test_full_size_workloads(p, logL, batch, variant):
+    torch = require_gpu()
+    L = 1 << logL
+    o = orc()
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    a = batch_inputs(600 + logL, batch, L, p)
+    fwd = run(plan, a, False, None, variant, torch)
+    assert np.array_equal(fwd.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64)))
+    back = run(plan, fwd, True, None, variant, torch)
+    want = (a.astype(object) * L % p).astype(np.uint64)
+    assert np.array_equal(back.astype(np.uint64), want), "inverse(forward(a)) != L a"
+    plan.destroy()
+
+
+def test_sampled_definition_c1():
+    """L = 2^10, p = 998244353: every output against the stored golden file and
+    sampled positions against the definition."""
+    torch = require_gpu()
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "forward_p998244353_L1024_seed1.txt")
+    g = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *v = line.split()
+        g[k] = [int(x) for x in v]
+    p, L, w = g["p"][0], g["L"][0], g["omega"][0]
+    assert ntt.root_of_unity(p, L) == w
+    plan = ntt.ntt_plan(p, w, L)
+    a = np.array(g["input"], dtype=np.uint32).reshape(1, L)
+    got = run(plan, a, False, None, 0, torch)
+    assert [int(v) for v in got[0]] == g["output"]
+    for k in (0, 1, 2, 511, 1023):
+        assert int(got[0, k]) == orc().dft_at(p, w, a[0], k)
+
+
+def test_transform_host_roundtrip():
+    require_gpu()
+    p, L = P_NTT30, 1 << 12
+    o = orc()
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    a = batch_inputs(700, 4, L, p)
+    h = a.copy()
+    ntt.ntt_transform_host(plan, False, h, 4)
+    assert np.array_equal(h.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64)))
+    ntt.ntt_transform_host(plan, True, h, 4)
+    assert np.array_equal(h.astype(np.uint64), (a.astype(object) * L % p).astype(np.uint64))
+
+
+def test_argument_errors():
+    torch = require_gpu()
+    p = P_NTT30
+    w = ntt.root_of_unity(p, 1024)
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan(p + 2, w, 1024)  # composite
+    assert e.value.code == -1
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan(p, w, 1000)
+    assert e.value.code == -2
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan(p, w, 1 << 24)  # 2^24 does not divide p-1
+    assert e.value.code == -2
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan(p, (w * w) % p, 1024)  # order 512
+    assert e.value.code == -3
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan((1 << 62) + 135, 3, 2)
+    assert e.value.code == -1
+    plan = ntt.ntt_plan(p, w, 1024)
+    d = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_forward_batch(plan, d.data_ptr() + 4, 1)
+    assert e.value.code == -8
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_forward_batch(plan, d, 1, 1000)
+    assert e.value.code == -4
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_forward_batch(plan, d, 0)
+    assert e.value.code == -4
+    for bad in ([5, 4], [2, 8], [11, 3], [3, 3, 2, 2]):  # wrong sum / pass too short / too long / tail < 2^5
+        with pytest.raises(ntt.NTTError) as e:
+            plan.set_split(bad)
+        assert e.value.code == -4
+    plan.destroy()
+
+
+def test_library_number_theory_matches_oracle():
+    require_gpu()
+    o = orc()
+    for p in (P_NTT30, P_NTT62) + P_UNEVEN:
+        for L in (2, 1024, 1 << 16):
+            assert ntt.root_of_unity(p, L) == o.root_of_unity(p, L)
+    assert ntt.find_prime(1 << 61, 24) == P_NTT62

@@ -1,0 +1,118 @@
+"""One persistent launch over many transforms of uneven lengths, primes and
+directions (ntt_execute_uneven): every result equals the oracle's transform of
+that vector alone; the launch can be captured in a CUDA graph and replayed;
+a wait that cannot be satisfied ends with NTT_ERR_TIMEOUT instead of a hang."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1205_2926_gb300 as ntt
+from paper_1205_2926_gb300.inputs import P_UNEVEN, P_NTT30, uneven_batch_spec, uniform_residues
+from tests.gpu_util import from_dev, require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+class Batch:
+    def __init__(self, spec, torch, seed=9):
+        o = oracle.get()
+        self.plans = {}
+        self.items = []
+        for d in spec:
+            L = 1 << d["logL"]
+            key = (d["p"], L)
+            if key not in self.plans:
+                self.plans[key] = ntt.ntt_plan(d["p"], o.root_of_unity(d["p"], L), L)
+            a = uniform_residues(seed * 100003 + d["id"], L, d["p"]).astype(np.uint32)
+            self.items.append((d, a, to_dev(a, torch)))
+
+    def descs(self):
+        return [(self.plans[(d["p"], 1 << d["logL"])], t, d["inverse"]) for d, _, t in self.items]
+
+    def check(self, rounds=1):
+        o = oracle.get()
+        for d, a, t in self.items:
+            L = 1 << d["logL"]
+            w = o.root_of_unity(d["p"], L)
+            want = a.astype(np.uint64)
+            for _ in range(rounds):
+                want = o.intt_ref(d["p"], w, want) if d["inverse"] else o.ntt_ref(d["p"], w, want)
+            got = from_dev(t, np.uint32).astype(np.uint64)
+            assert np.array_equal(got, want), f"transform {d['id']} (L=2^{d['logL']}, p={d['p']}, inv={d['inverse']})"
+
+
+def test_uneven_small_mix():
+    torch = require_gpu()
+    spec = uneven_batch_spec(seed=11, n=200, lmin=3, lmax=16)
+    b = Batch(spec, torch)
+    ntt.ntt_execute_uneven(b.descs())
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    b.check()
+
+
+def test_uneven_full_workload_4096():
+    """4096 transforms, L = 2^8..2^16 log-uniform, three 30-bit primes, half inverse."""
+    torch = require_gpu()
+    spec = uneven_batch_spec()
+    b = Batch(spec, torch)
+    ntt.ntt_execute_uneven(b.descs())
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    b.check()
+
+
+def test_uneven_graph_capture_and_replay():
+    torch = require_gpu()
+    spec = uneven_batch_spec(seed=12, n=120, lmin=8, lmax=15)
+    b = Batch(spec, torch)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ntt.ntt_execute_uneven(b.descs(), stream=s)  # warm-up: prepares and uploads the batch
+    torch.cuda.synchronize()
+    b.check(rounds=1)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ntt.ntt_execute_uneven(b.descs(), stream=s)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    b.check(rounds=3)
+
+
+def test_uneven_wait_times_out_with_status():
+    """A dependency that never completes: the bounded wait gives up, the launch
+    ends, the status says NTT_ERR_TIMEOUT and the context stays usable."""
+    torch = require_gpu()
+    spec = [{"id": 0, "logL": 16, "p": P_UNEVEN[0], "inverse": False},
+            {"id": 1, "logL": 14, "p": P_UNEVEN[1], "inverse": True}]
+    b = Batch(spec, torch)
+    try:
+        ntt.ntt_uneven_set_wait_budget(20_000_000, stall_stage=1)  # ~10 ms
+        ntt.ntt_execute_uneven(b.descs())
+        torch.cuda.synchronize()
+        assert ntt.ntt_uneven_status() == -7
+    finally:
+        ntt.ntt_uneven_set_wait_budget(2_000_000_000, stall_stage=-1)
+    b2 = Batch(spec, torch, seed=10)
+    ntt.ntt_execute_uneven(b2.descs())
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    b2.check()
+
+
+def test_uneven_rejects_unsupported():
+    torch = require_gpu()
+    from paper_1205_2926_gb300.inputs import P_NTT62
+    o = oracle.get()
+    plan64 = ntt.ntt_plan(P_NTT62, o.root_of_unity(P_NTT62, 1024), 1024)
+    t = torch.zeros(2048, dtype=torch.int64, device="cuda")
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_execute_uneven([(plan64, t, False)])
+    assert e.value.code == -9
+    plan = ntt.ntt_plan(P_NTT30, o.root_of_unity(P_NTT30, 1024), 1024)
+    t32 = torch.zeros(2048, dtype=torch.int32, device="cuda")
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_execute_uneven([(plan, t32.data_ptr() + 4, False)])
+    assert e.value.code == -8

@@ -1,0 +1,38 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/ntt_gb300.h declares (no compute calls)."""
+import os
+import re
+
+import paper_1205_2926_gb300 as ntt
+from paper_1205_2926_gb300 import build as b
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\**\s*(\w+)\s*\(", text, flags=re.M):
+            if m.group(1) not in ("if", "while", "for", "return", "sizeof"):
+                names.append(m.group(1))
+    return names
+
+
+def test_library_exports_declared_symbols():
+    b.build()
+    lib = ntt._lib.load()
+    names = declared_functions()
+    assert "ntt_plan" in names and "polymul_mod_p" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+    assert lib.ntt_version() >= 100
+    assert lib.ntt_strerror(-3).decode().startswith("omega")
+
+
+def test_binding_covers_declared_symbols():
+    names = set(declared_functions())
+    assert names <= set(ntt._lib.exported_symbols()), names - set(ntt._lib.exported_symbols())
