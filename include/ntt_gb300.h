@@ -164,6 +164,37 @@ int ntt_transform_host(ntt_plan_t plan, int inverse, void *h_data, size_t batch,
  * p-1), NTT_ERR_MODULUS, NTT_ERR_ALIGN, NTT_ERR_NOMEM, NTT_ERR_CUDA. */
 int polymul_mod_p(uint64_t p, const void *d_a, size_t na, const void *d_b, size_t nb, void *d_c, void *stream);
 
+/* Size of the fixed device scratch of polymul_mod_p_noalloc, in bytes. */
+#define NTT_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* polymul_mod_p for callers that must not allocate device memory while they
+ * run.  The paper has no counterpart; this is a library-level variant.  Who
+ * needs it: code whose device memory belongs to another allocator (a
+ * framework's caching allocator or a fixed arena) and may not allocate
+ * behind its back, and latency-critical paths where a cudaMalloc or
+ * cudaMallocAsync could block, synchronise or fail under memory pressure.
+ * This call allocates nothing: its scratch (the two zero-padded operands,
+ * 2 L words) is a file-scope __device__ array of NTT_NOALLOC_SCRATCH_BYTES
+ * (8 MiB) that every GPU loading the library holds until the process exits.
+ * Sizes: 2 * L * word_bytes must fit, i.e. L <= 2^20 for 32-bit words and
+ * L <= 2^19 for 64-bit words; larger requests return NTT_ERR_RANGE.
+ * `plan` is made beforehand with ntt_plan (that call does allocate, so make
+ * it at set-up time) for the modulus, any primitive L-th root and a length
+ * L >= na + nb - 1; it must use NTT_VARIANT_LAZY and belong to the current
+ * device.  a, b, c are device arrays as for polymul_mod_p; the result equals
+ * polymul_mod_p's.  The first call on a device looks up the address of the
+ * scratch array for that device (set-up done once per device); make that
+ * first call before any stream capture.  Every call on a device shares the
+ * one scratch array and leaves its contents behind (each call rewrites all
+ * of it before use): calls whose work overlaps on the GPU -- different
+ * streams, or different host threads -- race and give wrong results, so
+ * serialise them (one stream, or events).  Asynchronous on `stream`.
+ * Errors: NTT_ERR_ARG (null pointer, na or nb zero, NTL plan, plan of
+ * another device), NTT_ERR_LENGTH (L < na + nb - 1), NTT_ERR_RANGE (scratch
+ * too small), NTT_ERR_ALIGN, NTT_ERR_CUDA. */
+int polymul_mod_p_noalloc(ntt_plan_t plan, const void *d_a, size_t na, const void *d_b, size_t nb, void *d_c,
+                          void *stream);
+
 /* ------------------------------------------------------------- uneven batch */
 
 /* One transform of an uneven batch: its plan, its device vector (L words of

@@ -139,6 +139,13 @@ def polymul_mod_p(p: int, a, na: int, b, nb: int, c, stream=None) -> None:
     check(_lib.load().polymul_mod_p(p, _ptr(a), na, _ptr(b), nb, _ptr(c), _stream(stream)), "polymul_mod_p")
 
 
+def polymul_mod_p_noalloc(plan: Plan, a, na: int, b, nb: int, c, stream=None) -> None:
+    """polymul_mod_p with a plan made beforehand and the library's fixed device
+    scratch: allocates nothing (see the C header for the limits)."""
+    check(_lib.load().polymul_mod_p_noalloc(plan.handle, _ptr(a), na, _ptr(b), nb, _ptr(c), _stream(stream)),
+          "polymul_mod_p_noalloc")
+
+
 def ntt_execute_uneven(descs, stream=None) -> None:
     """descs: sequence of (plan, device tensor or pointer, inverse flag)."""
     n = len(descs)

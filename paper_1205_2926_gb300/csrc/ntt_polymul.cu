@@ -145,3 +145,48 @@ extern "C" int polymul_mod_p(uint64_t p, const void *d_a, size_t na, const void 
     if (rc) return rc;
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "cudaFreeAsync");
 }
+
+// ---------------------------------------------------------------------------
+// polymul_mod_p without any allocation.  Its scratch lives in a file-scope
+// __device__ array; host code cannot use the array's name as a device
+// address (on the host the name is only a stand-in), so the address is
+// looked up with cudaGetSymbolAddress once per device, with that device
+// current, and passed to the kernels.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NTT_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64];
+
+static int noalloc_scratch(int dev, void **out) {
+    if (dev < 0 || dev >= 64) return NTT_ERR_RANGE;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                       "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return NTT_OK;
+}
+
+extern "C" int polymul_mod_p_noalloc(ntt_plan_t plan, const void *d_a, size_t na, const void *d_b, size_t nb,
+                                     void *d_c, void *stream) {
+    if (!plan || !d_a || !d_b || !d_c || na == 0 || nb == 0) return NTT_ERR_ARG;
+    if (plan->variant != NTT_VARIANT_LAZY) return NTT_ERR_ARG;
+    const uint64_t n = (uint64_t)na + nb - 1;
+    if (n > plan->L) return NTT_ERR_LENGTH;
+    const size_t wb = (size_t)plan->wbytes;
+    if (2 * plan->L * wb > (uint64_t)NTT_NOALLOC_SCRATCH_BYTES) return NTT_ERR_RANGE;
+    if (((uintptr_t)d_a | (uintptr_t)d_b | (uintptr_t)d_c) & (wb - 1)) return NTT_ERR_ALIGN;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != plan->device) return NTT_ERR_ARG;
+    void *buf = nullptr;
+    int rc = noalloc_scratch(dev, &buf);
+    if (rc) return rc;
+    return enqueue_polymul(plan, d_a, na, d_b, nb, d_c, buf, (cudaStream_t)stream);
+}
