@@ -64,14 +64,21 @@ struct LaunchSpec {
     uint64_t stride;
     uint32_t batch;
     int logL, logR, logS, logTV, logTA;
-    int per_cta;
+    int per_cta;          // column pass: sub-tiles per CTA iteration; row pass: rows per iteration
+    uint32_t ntiles;      // CTA iterations of the pass
+    uint32_t buf_chunks;  // 16-byte chunks of one shared-memory tile buffer
     uint32_t flags;
     const void *tw, *ma, *mb;
     uint64_t p;
     uint64_t nrows;
-    unsigned grid;
-    size_t smem;
+    unsigned grid;  // tiny kernel only
+    size_t smem;    // dynamic shared memory of the launch
 };
+
+// Tile geometry of pass q of a plan for a batch (or, for a row pass over
+// single-row transforms, `rows` rows): fills logTV, per_cta, ntiles,
+// buf_chunks and nrows of the spec.
+void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s);
 cudaError_t launch_pass_u32(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
 cudaError_t launch_pass_u64(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
 

@@ -16,17 +16,29 @@
 //
 // Stage twiddles.  In an R-point sub-transform the stage of distance m uses
 // omega_R^(k R / 2m) = omega^(k L / 2m): the same value as in the full-length
-// Algorithm 1, independent of R.  One table tw[m - 1 + k] = (W, W') for
-// k < m, m = 1, 2, 4, ... serves every pass (Shoup quotients W' =
-// floor(W beta / p), Algorithms 2-4).
+// Algorithm 1, independent of R.  One table tw[m + k] = (W, W') for k < m,
+// m = 1, 2, 4, ... (entry 0 unused) serves every pass; W' = floor(W beta/p)
+// is the precomputed Shoup quotient of Algorithms 2-4.  The offset m (rather
+// than m - 1) keeps runs of consecutive k 16-byte aligned for vector loads.
 //
-// On-chip work.  A CTA stages its tile in shared memory as 16-byte vectors
-// of V words (V = 4 for 32-bit, 2 for 64-bit words); the V words of a vector
-// belong to V independent sub-transforms that share every twiddle.  Each
-// thread works on E = 8 vectors at a time in registers (a radix-8 block: up
-// to three butterfly stages per round), then writes them back; rounds are
-// separated by __syncthreads().  Global loads and stores are 16-byte and
-// coalesced.
+// On-chip work.  A CTA stages a tile in shared memory as 16-byte vectors of
+// V words (V = 4 for 32-bit, 2 for 64-bit words):
+//   column pass: a vector holds V adjacent columns, i.e. the same element of
+//     V independent sub-transforms, which share every twiddle;
+//   row pass: a vector holds V consecutive elements of one row; the stages
+//     on the low log2(V) index bits run inside the vector ("lane stages"),
+//     the others on whole vectors with one twiddle per lane.
+// Each thread holds E = 8 vectors in registers and runs up to three
+// butterfly stages per round (radix-8 blocks); rounds exchange vectors
+// through shared memory.  The vector of row s sits at chunk
+// TV*(s + (s >> 3)) + tv (one padding chunk per eight): in every round the
+// eight threads of a quarter-warp hit eight distinct bank groups, and the
+// eight chunks of one thread sit at compile-time offsets from one base.
+//
+// Pipeline.  CTAs are persistent: each walks its tiles with stride gridDim.x
+// and prefetches the next tile with cp.async (16-byte global-to-shared
+// copies that bypass L1) into a second buffer while it computes the current
+// one, so HBM traffic overlaps the butterflies.
 //
 // Butterflies: Algorithm 3 / Algorithm 4 (lazy, redundant [0,2p) / [0,4p))
 // or Algorithm 2 / its fully reduced inverse (the NTL-style baseline).
@@ -44,8 +56,6 @@ enum { VAR_LAZY = 0, VAR_NTL = 1 };
 enum { F_NORMALIZE = 1, F_MIDDLE = 2, F_MB = 4 };
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels
-constexpr int kE = 8;          // vectors per thread per round (radix-8 blocks)
-constexpr int kLogE = 3;
 
 template <typename W>
 struct Lanes {
@@ -56,41 +66,78 @@ struct Lanes {
 // Arguments of one pass over a batch of transforms.
 template <typename W>
 struct PassArgs {
-    W *data;          // transform 0
-    uint64_t stride;  // words between consecutive transforms
+    W *data;              // transform 0
+    uint64_t stride;      // words between consecutive transforms
     uint32_t batch;
     int32_t logL;
-    int32_t logR;     // sub-transform length of this pass
-    int32_t logS;     // column stride (0 for the contiguous row pass)
-    int32_t per_cta;  // column pass: tiles per CTA; row pass: vector groups per CTA
-    int32_t logTV;    // column pass: 16-byte vectors per tile row (tile width T = TV * V words)
-    int32_t logTA;    // column pass: width of the middle-twiddle table MA (TA >= T)
-    uint32_t flags;   // F_NORMALIZE | F_MIDDLE | F_MB
-    const W *tw;      // stage twiddle pairs, forward or inverse roots
-    const W *ma;      // middle twiddle pairs MA[s][c mod TA]
-    const W *mb;      // middle twiddle pairs MB[c / TA][s]
+    int32_t logS;         // column stride of a column pass (0 for the row pass)
+    int32_t logTV;        // column pass: 16-byte vectors per tile row
+    int32_t logTA;        // column pass: width of the middle-twiddle table MA
+    int32_t per_cta;      // column pass: tiles per CTA iteration; row pass: rows per iteration
+    uint32_t ntiles;      // CTA iterations in this pass
+    uint32_t buf_chunks;  // 16-byte chunks of one shared-memory buffer
+    uint32_t flags;       // F_NORMALIZE | F_MIDDLE | F_MB
+    const W *tw;          // stage twiddle pairs tw[m + k], forward or inverse roots
+    const W *ma;          // middle twiddle pairs MA[s][c mod TA]
+    const W *mb;          // middle twiddle pairs MB[c / TA][s]
     W p;
-    uint64_t nrows;   // row pass: number of rows (batch * L / R)
-    W *const *rowptrs;  // row pass over single-row transforms: address of each row (else null)
+    uint64_t nrows;       // row pass: number of rows (batch * L / R, or transforms)
+    W *const *rowptrs;    // row pass over single-row transforms: address of each row (else null)
 };
 
+// ------------------------------------------------------------- small helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(uint4 *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <typename W>
-__device__ __forceinline__ void load_pair(const W *__restrict__ t, uint32_t idx, W &w, W &wq);
+__device__ __forceinline__ void ld_pair(const W *__restrict__ t, int idx, W &w, W &wq);
 
 template <>
-__device__ __forceinline__ void load_pair<uint32_t>(const uint32_t *__restrict__ t, uint32_t idx, uint32_t &w,
-                                                    uint32_t &wq) {
+__device__ __forceinline__ void ld_pair<uint32_t>(const uint32_t *__restrict__ t, int idx, uint32_t &w,
+                                                  uint32_t &wq) {
     uint2 v = __ldg(reinterpret_cast<const uint2 *>(t) + idx);
     w = v.x;
     wq = v.y;
 }
 
 template <>
-__device__ __forceinline__ void load_pair<uint64_t>(const uint64_t *__restrict__ t, uint32_t idx, uint64_t &w,
-                                                    uint64_t &wq) {
+__device__ __forceinline__ void ld_pair<uint64_t>(const uint64_t *__restrict__ t, int idx, uint64_t &w,
+                                                  uint64_t &wq) {
     ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(t) + idx);
     w = v.x;
     wq = v.y;
+}
+
+// V consecutive pairs starting at pair index idx (a multiple of V, so that
+// the two 16-byte loads are aligned).
+template <typename W>
+__device__ __forceinline__ void ld_pairs(const W *__restrict__ t, int idx, W (&w)[Lanes<W>::V],
+                                         W (&wq)[Lanes<W>::V]);
+
+template <>
+__device__ __forceinline__ void ld_pairs<uint32_t>(const uint32_t *__restrict__ t, int idx, uint32_t (&w)[4],
+                                                   uint32_t (&wq)[4]) {
+    const uint4 *q = reinterpret_cast<const uint4 *>(t + 2 * idx);
+    const uint4 a = __ldg(q), b = __ldg(q + 1);
+    w[0] = a.x, wq[0] = a.y, w[1] = a.z, wq[1] = a.w;
+    w[2] = b.x, wq[2] = b.y, w[3] = b.z, wq[3] = b.w;
+}
+
+template <>
+__device__ __forceinline__ void ld_pairs<uint64_t>(const uint64_t *__restrict__ t, int idx, uint64_t (&w)[2],
+                                                   uint64_t (&wq)[2]) {
+    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(t) + idx;
+    const ulonglong2 a = __ldg(q), b = __ldg(q + 1);
+    w[0] = a.x, wq[0] = a.y, w[1] = b.x, wq[1] = b.y;
 }
 
 template <typename W>
@@ -109,82 +156,18 @@ __device__ __forceinline__ uint4 pack(const W (&x)[Lanes<W>::V]) {
     return c;
 }
 
-// Round geometry: the thread's E vectors are s_j = hi | (j << b0) | lo with
-// (hi, lo) taken from the unit index g; the round executes `nst` of the
-// three stage bits b0+2, b0+1, b0 (the top ones when nst < 3).
-struct Round {
-    int b0, nst;
-};
-
-__device__ __forceinline__ Round round_geometry(int dir, int r, int nrounds, int logR) {
-    int e0 = logR - kLogE * (nrounds - 1);  // 1..3 stages in the partial round
-    Round g;
-    if (dir == DIR_FWD) {
-        g.b0 = r == 0 ? logR - kLogE : logR - e0 - kLogE * r;
-        g.nst = r == 0 ? e0 : kLogE;
-    } else {
-        g.b0 = r == nrounds - 1 ? logR - kLogE : kLogE * r;
-        g.nst = r == nrounds - 1 ? e0 : kLogE;
-    }
-    return g;
-}
-
-__device__ __forceinline__ uint32_t elem_index(uint32_t g, int b0, int j) {
-    uint32_t lo = g & ((1u << b0) - 1u);
-    return ((g >> b0) << (b0 + kLogE)) | ((uint32_t)j << b0) | lo;
-}
-
-// Butterfly stages of one round on E vectors held in registers.
 template <typename W, int DIR, int VAR>
-__device__ __forceinline__ void round_stages(W (&x)[kE][Lanes<W>::V], int b0, int nst, uint32_t lo,
-                                             const W *__restrict__ tw, W p, W p2) {
-    constexpr int V = Lanes<W>::V;
+__device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2) {
     if (DIR == DIR_FWD) {
-#pragma unroll
-        for (int lb = kLogE - 1; lb >= 0; --lb) {
-            if (lb >= kLogE - nst) {
-#pragma unroll
-                for (int jl = 0; jl < (1 << lb); ++jl) {
-                    uint32_t idx = (1u << (b0 + lb)) - 1u + (((uint32_t)jl << b0) | lo);
-                    W w, wq;
-                    load_pair(tw, idx, w, wq);
-#pragma unroll
-                    for (int jh = 0; jh < kE; jh += (2 << lb)) {
-                        const int j = jh + jl, j2 = j + (1 << lb);
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            if (VAR == VAR_LAZY)
-                                bfly_fwd_lazy(x[j][v], x[j2][v], w, wq, p, p2);
-                            else
-                                bfly_fwd_ntl(x[j][v], x[j2][v], w, wq, p);
-                        }
-                    }
-                }
-            }
-        }
+        if (VAR == VAR_LAZY)
+            bfly_fwd_lazy(x, y, w, wq, p, p2);
+        else
+            bfly_fwd_ntl(x, y, w, wq, p);
     } else {
-#pragma unroll
-        for (int lb = 0; lb < kLogE; ++lb) {
-            if (lb >= kLogE - nst) {
-#pragma unroll
-                for (int jl = 0; jl < (1 << lb); ++jl) {
-                    uint32_t idx = (1u << (b0 + lb)) - 1u + (((uint32_t)jl << b0) | lo);
-                    W w, wq;
-                    load_pair(tw, idx, w, wq);
-#pragma unroll
-                    for (int jh = 0; jh < kE; jh += (2 << lb)) {
-                        const int j = jh + jl, j2 = j + (1 << lb);
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            if (VAR == VAR_LAZY)
-                                bfly_inv_lazy(x[j][v], x[j2][v], w, wq, p, p2);
-                            else
-                                bfly_inv_ntl(x[j][v], x[j2][v], w, wq, p);
-                        }
-                    }
-                }
-            }
-        }
+        if (VAR == VAR_LAZY)
+            bfly_inv_lazy(x, y, w, wq, p, p2);
+        else
+            bfly_inv_ntl(x, y, w, wq, p);
     }
 }
 
@@ -194,218 +177,315 @@ __device__ __forceinline__ W mul_twiddle(W x, W w, W wq, W p) {
     return VAR == VAR_NTL ? csub(y, p) : y;
 }
 
-// Middle twiddle of a column pass, omega^((L/B) c rev(s)), on the E vectors
-// of rows s = 8 g + j (the round with b0 = 0), columns
-// c = ct*T + tv*V + v.  It is factored as MB[c >> logTA][s] * MA[s][c mod TA]
-// (two Shoup products) so that both tables stay near 2 R sqrt(S) entries.
-template <typename W, int VAR>
-__device__ __forceinline__ void middle_twiddle(W (&x)[kE][Lanes<W>::V], uint32_t g, uint32_t tv, uint32_t ct,
-                                               const PassArgs<W> &a) {
-    constexpr int V = Lanes<W>::V;
-    const uint32_t R = 1u << a.logR;
-    const uint32_t c0 = (ct << (a.logTV + Lanes<W>::LOGV)) + tv * V;  // first column of this vector
-    const uint32_t TAm = (1u << a.logTA) - 1u;
-    const uint32_t chi = c0 >> a.logTA;
-#pragma unroll
-    for (int j = 0; j < kE; ++j) {
-        const uint32_t s = (g << kLogE) | j;
-        if (a.flags & F_MB) {
-            W w, wq;
-            load_pair(a.mb, chi * R + s, w, wq);
-#pragma unroll
-            for (int v = 0; v < V; ++v) x[j][v] = mul_twiddle<W, VAR>(x[j][v], w, wq, a.p);
-        }
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            W w, wq;
-            load_pair(a.ma, (s << a.logTA) + ((c0 + v) & TAm), w, wq);
-            x[j][v] = mul_twiddle<W, VAR>(x[j][v], w, wq, a.p);
-        }
+// ------------------------------------------------------- compile-time rounds
+//
+// LOGS vector-index bits are handled by rounds of up to LE = 3 stages.  In
+// round r the thread's E vectors are s_j = hi | (j << b0) | lo, with (hi, lo)
+// taken from the unit's group index g; the round executes `nst` of its local
+// stage bits (the top ones when the partial round has fewer than LE).
+template <int LOGS>
+struct Sched {
+    static constexpr int LE = LOGS < 3 ? LOGS : 3;
+    static constexpr int E = 1 << LE;
+    static constexpr int NR = (LOGS + LE - 1) / LE;
+    static constexpr int E0 = LOGS - LE * (NR - 1);
+    __host__ __device__ static constexpr int b0(int dir, int r) {
+        return dir == DIR_FWD ? (r == 0 ? LOGS - LE : LOGS - E0 - LE * r) : (r == NR - 1 ? LOGS - LE : LE * r);
     }
-}
-
-template <typename W, int DIR, int VAR>
-__device__ __forceinline__ void normalize(W (&x)[kE][Lanes<W>::V], W p, W p2) {
-#pragma unroll
-    for (int j = 0; j < kE; ++j)
-#pragma unroll
-        for (int v = 0; v < Lanes<W>::V; ++v) {
-            if (VAR == VAR_LAZY) x[j][v] = DIR == DIR_FWD ? reduce2(x[j][v], p) : reduce4(x[j][v], p, p2);
-        }
-}
-
-__device__ __forceinline__ uint4 ldg16(const void *p) { return *reinterpret_cast<const uint4 *>(p); }
-// Load that bypasses L1: data written earlier in the same launch by other
-// CTAs (the persistent uneven-batch kernel) must not be served from a stale
-// L1 line.
-__device__ __forceinline__ uint4 ldcg16(const void *p) { return __ldcg(reinterpret_cast<const uint4 *>(p)); }
-__device__ __forceinline__ void stg16(void *p, const uint4 &v) { *reinterpret_cast<uint4 *>(p) = v; }
-
-// ---------------------------------------------------------------------------
-// Shared-memory layout of a tile: R rows (elements s of the sub-transforms)
-// x TV 16-byte vectors per row.  Vector (s, tv) sits at chunk
-//     (s*TV + tv) ^ (((s >> 3) * TV) & 7),
-// an XOR swizzle inside aligned groups of 8 chunks.  For TV in {1,2,4,8} and
-// every round geometry, the 8 threads of a quarter-warp then touch 8
-// distinct bank groups, so the 16-byte shared loads and stores of the
-// rounds are conflict-free (checked exhaustively for R = 2^3 .. 2^12).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t chunk_at(uint32_t s, uint32_t tv, int logTV) {
-    return ((s << logTV) + tv) ^ (((s >> 3) << logTV) & 7u);
-}
-
-// Column pass (ROW = false): a tile is R rows x TV vectors (T = TV*V
-// consecutive columns) of one block; global row s of the tile is TV*16
-// contiguous bytes.  Row pass (ROW = true, TV = 1): a "vector group" is V
-// consecutive rows of length R, vector s holding element s of each.
-template <typename W>
-__device__ __forceinline__ W *row_ptr(const PassArgs<W> &a, uint64_t row) {
-    if (a.rowptrs) return a.rowptrs[row];
-    const int shift = a.logL - a.logR;  // rows per transform = 2^shift
-    const uint64_t b = row >> shift, within = row & ((1ull << shift) - 1ull);
-    return a.data + b * a.stride + (within << a.logR);
-}
-
-template <typename W, bool STORE, bool COH>
-__device__ __forceinline__ void row_copy(const PassArgs<W> &a, uint4 *sm, uint64_t row0, int groups) {
-    constexpr int V = Lanes<W>::V, LOGV = Lanes<W>::LOGV;
-    const int logR = a.logR;
-    const uint32_t R = 1u << logR;
-    const int logn16 = logR - LOGV;             // 16-byte chunks per row
-    const uint32_t total = (uint32_t)groups << logR;  // groups * V rows * R/V chunks
-    for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
-        uint32_t c, v, grp;
-        if (logn16 >= 3) {  // 8 consecutive threads cover 128 contiguous bytes of one row
-            c = (i & 7) | (((i >> (3 + LOGV)) & ((1u << (logn16 - 3)) - 1)) << 3);
-            v = (i >> 3) & (V - 1);
-        } else {
-            c = i & ((1u << logn16) - 1);
-            v = (i >> logn16) & (V - 1);
-        }
-        grp = i >> logR;
-        const uint64_t row = row0 + grp * V + v;
-        if (row >= a.nrows) continue;
-        W *g = row_ptr(a, row) + c * V;
-        W *base = reinterpret_cast<W *>(sm + grp * R);
-        if (!STORE) {
-            uint4 q = COH ? ldcg16(g) : ldg16(g);
-            const W *pq = reinterpret_cast<const W *>(&q);
-#pragma unroll
-            for (int k = 0; k < V; ++k) base[chunk_at(c * V + k, 0, 0) * V + v] = pq[k];
-        } else {
-            uint4 q;
-            W *pq = reinterpret_cast<W *>(&q);
-#pragma unroll
-            for (int k = 0; k < V; ++k) pq[k] = base[chunk_at(c * V + k, 0, 0) * V + v];
-            stg16(g, q);
-        }
-    }
-}
-
-// Tile t of a column pass -> (transform b, block blk, column tile ct); all
-// counts are powers of two: 2^ltb tiles per block, 2^lbt blocks per transform.
-template <typename W>
-struct ColTile {
-    int ltb, lbt;
-    __device__ __forceinline__ W *origin(const PassArgs<W> &a, uint32_t t, uint32_t &ct) const {
-        ct = t & ((1u << ltb) - 1u);
-        const uint32_t blk = (t >> ltb) & ((1u << lbt) - 1u), b = t >> (ltb + lbt);
-        return a.data + (uint64_t)b * a.stride + ((uint64_t)blk << (a.logR + a.logS)) +
-               ((uint64_t)ct << (a.logTV + Lanes<W>::LOGV));
+    __host__ __device__ static constexpr int nst(int dir, int r) {
+        return dir == DIR_FWD ? (r == 0 ? E0 : LE) : (r == NR - 1 ? E0 : LE);
     }
 };
 
-template <typename W, bool STORE, bool COH>
-__device__ __forceinline__ void col_copy(const PassArgs<W> &a, uint4 *sm, const ColTile<W> &ct_info, uint32_t tile0,
-                                         int ntile) {
+// Butterfly stages of one round on E vectors held in registers.  twp points
+// at tw + (low index bits of the unit); QUAD takes one twiddle per lane.
+template <typename W, int DIR, int VAR, int LE, int B0, int NST, bool QUAD>
+__device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W *__restrict__ twp, W p, W p2) {
     constexpr int V = Lanes<W>::V;
-    const int logR = a.logR, logTV = a.logTV;
-    const uint32_t R = 1u << logR, TV = 1u << logTV;
-    const uint64_t S = 1ull << a.logS;
-    const uint32_t total = (uint32_t)ntile << (logR + logTV);
-    for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
-        const uint32_t cc = i & (TV - 1), s = (i >> logTV) & (R - 1), ti = i >> (logTV + logR);
-        uint32_t ct;
-        W *g = ct_info.origin(a, tile0 + ti, ct) + s * S + cc * V;
-        uint4 *slot = sm + (ti << (logR + logTV)) + chunk_at(s, cc, logTV);
-        if (!STORE)
-            *slot = COH ? ldcg16(g) : ldg16(g);
-        else
-            stg16(g, *slot);
-    }
-}
-
-// The work of one CTA in one pass.  Column pass: CTA `cta` takes tiles
-// cta*per_cta ...; row pass: vector groups cta*per_cta ... (per_cta * V
-// rows).  Unit u of a round -> (tile or group ti, vector tv, element group g).
-// COH selects L1-bypassing loads (needed when other CTAs of the same launch
-// produced the input).
-template <typename W, int DIR, int VAR, bool ROW, bool COH>
-__device__ __forceinline__ void pass_cta(const PassArgs<W> &a, uint32_t cta, uint4 *sm) {
-    constexpr int V = Lanes<W>::V;
-    const int logR = a.logR;
-    const int logTV = ROW ? 0 : a.logTV;
-    const uint32_t R = 1u << logR;
-    const W p = a.p, p2 = (W)(2 * a.p);
-    const int nrounds = (logR + kLogE - 1) / kLogE;
-
-    ColTile<W> cti;
-    cti.ltb = 0;
-    uint32_t tile0 = 0;
-    int ntile = a.per_cta;
-    uint64_t row0 = 0;
-    if (ROW) {
-        row0 = (uint64_t)cta * a.per_cta * V;
-        row_copy<W, false, COH>(a, sm, row0, a.per_cta);
-    } else {
-        cti.ltb = a.logS - a.logTV - Lanes<W>::LOGV;
-        cti.lbt = a.logL - logR - a.logS;
-        const uint32_t tiles_total = a.batch << (cti.ltb + cti.lbt);
-        tile0 = cta * a.per_cta;
-        ntile = min((uint32_t)a.per_cta, tiles_total - tile0);
-        col_copy<W, false, COH>(a, sm, cti, tile0, ntile);
-    }
-    __syncthreads();
-
-    const uint32_t units = (uint32_t)ntile << (logR - kLogE + logTV);
-    for (int r = 0; r < nrounds; ++r) {
-        const Round rg = round_geometry(DIR, r, nrounds, logR);
-        for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
-            const uint32_t tv = u & ((1u << logTV) - 1u);
-            const uint32_t g = (u >> logTV) & ((R >> kLogE) - 1u);
-            const uint32_t ti = u >> (logTV + logR - kLogE);
-            uint4 *tsm = sm + (ti << (logR + logTV));
-            W x[kE][V];
+    constexpr int E = 1 << LE;
+    constexpr int B0S = QUAD ? B0 + Lanes<W>::LOGV : B0;  // bit position in element-index space
 #pragma unroll
-            for (int j = 0; j < kE; ++j) unpack(tsm[chunk_at(elem_index(g, rg.b0, j), tv, logTV)], x[j]);
-            if (!ROW && (a.flags & F_MIDDLE) && ((DIR == DIR_INV && r == 0) || (DIR == DIR_FWD && r == nrounds - 1))) {
-                if (DIR == DIR_FWD)
-                    round_stages<W, DIR, VAR>(x, rg.b0, rg.nst, g & ((1u << rg.b0) - 1u), a.tw, p, p2);
-                const uint32_t ct = (tile0 + ti) & ((1u << cti.ltb) - 1u);
-                middle_twiddle<W, VAR>(x, g, tv, ct, a);
-                if (DIR == DIR_INV)
-                    round_stages<W, DIR, VAR>(x, rg.b0, rg.nst, g & ((1u << rg.b0) - 1u), a.tw, p, p2);
+    for (int step = 0; step < NST; ++step) {
+        const int lb = DIR == DIR_FWD ? LE - 1 - step : LE - NST + step;
+#pragma unroll
+        for (int jl = 0; jl < (1 << lb); ++jl) {
+            const int off = (1 << (B0S + lb)) + (jl << B0S);
+            if (!QUAD) {
+                W w, wq;
+                ld_pair(twp, off, w, wq);
+#pragma unroll
+                for (int jh = 0; jh < E; jh += (2 << lb)) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        bfly<W, DIR, VAR>(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w, wq, p, p2);
+                }
             } else {
-                round_stages<W, DIR, VAR>(x, rg.b0, rg.nst, g & ((1u << rg.b0) - 1u), a.tw, p, p2);
-            }
-            if (r == nrounds - 1 && (a.flags & F_NORMALIZE)) normalize<W, DIR, VAR>(x, p, p2);
+                W w[V], wq[V];
+                ld_pairs<W>(twp, off, w, wq);
 #pragma unroll
-            for (int j = 0; j < kE; ++j) tsm[chunk_at(elem_index(g, rg.b0, j), tv, logTV)] = pack<W>(x[j]);
+                for (int jh = 0; jh < E; jh += (2 << lb)) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        bfly<W, DIR, VAR>(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w[v], wq[v], p, p2);
+                }
+            }
         }
-        __syncthreads();
     }
-
-    if (ROW)
-        row_copy<W, true, COH>(a, sm, row0, a.per_cta);
-    else
-        col_copy<W, true, COH>(a, sm, cti, tile0, ntile);
 }
 
-// One pass over a batch, one CTA per `per_cta` tiles (or groups).
-template <typename W, int DIR, int VAR, bool ROW>
+// Twiddles of the lane stages (element-index bits below log2 V): tw[1]
+// (distance 1) and tw[2], tw[3] (distance 2, 32-bit words only).
+template <typename W>
+struct LaneTw {
+    W w[3], wq[3];
+};
+
+template <typename W, int DIR, int VAR, int E>
+__device__ __forceinline__ void lane_stages(W (&x)[E][Lanes<W>::V], const LaneTw<W> &lt, W p, W p2) {
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        if (Lanes<W>::V == 4) {
+            if (DIR == DIR_FWD) {
+                bfly<W, DIR, VAR>(x[j][0], x[j][2], lt.w[1], lt.wq[1], p, p2);
+                bfly<W, DIR, VAR>(x[j][1], x[j][3], lt.w[2], lt.wq[2], p, p2);
+                bfly<W, DIR, VAR>(x[j][0], x[j][1], lt.w[0], lt.wq[0], p, p2);
+                bfly<W, DIR, VAR>(x[j][2], x[j][3], lt.w[0], lt.wq[0], p, p2);
+            } else {
+                bfly<W, DIR, VAR>(x[j][0], x[j][1], lt.w[0], lt.wq[0], p, p2);
+                bfly<W, DIR, VAR>(x[j][2], x[j][3], lt.w[0], lt.wq[0], p, p2);
+                bfly<W, DIR, VAR>(x[j][0], x[j][2], lt.w[1], lt.wq[1], p, p2);
+                bfly<W, DIR, VAR>(x[j][1], x[j][3], lt.w[2], lt.wq[2], p, p2);
+            }
+        } else {
+            bfly<W, DIR, VAR>(x[j][0], x[j][1], lt.w[0], lt.wq[0], p, p2);
+        }
+    }
+}
+
+template <typename W, int DIR, int VAR, int E>
+__device__ __forceinline__ void normalize(W (&x)[E][Lanes<W>::V], W p, W p2) {
+    if (VAR != VAR_LAZY) return;
+#pragma unroll
+    for (int j = 0; j < E; ++j)
+#pragma unroll
+        for (int v = 0; v < Lanes<W>::V; ++v)
+            x[j][v] = DIR == DIR_FWD ? reduce2(x[j][v], p) : reduce4(x[j][v], p, p2);
+}
+
+// Middle twiddle of a column pass, omega^((L/B) c rev(s)), on the E vectors
+// of rows s = s0 + j (the round with b0 = 0), columns c = c0 + v.  Factored
+// as MB[c >> logTA][s] * MA[s][c mod TA]: two Shoup products from two small
+// tables (about 2 R sqrt(S) entries in all) instead of one table of B.
+template <typename W, int VAR, int E>
+__device__ __forceinline__ void middle_twiddle(W (&x)[E][Lanes<W>::V], uint32_t s0, uint32_t c0, uint32_t R,
+                                               const PassArgs<W> &a) {
+    constexpr int V = Lanes<W>::V;
+    const uint32_t TAm = (1u << a.logTA) - 1u;
+    const W *mbp = a.mb + 2 * ((uint64_t)(c0 >> a.logTA) * R + s0);
+    const W *map = a.ma + 2 * (((uint64_t)s0 << a.logTA) + (c0 & TAm));
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        if (a.flags & F_MB) {
+            W w, wq;
+            ld_pair(mbp, j, w, wq);
+#pragma unroll
+            for (int v = 0; v < V; ++v) x[j][v] = mul_twiddle<W, VAR>(x[j][v], w, wq, a.p);
+        }
+        W w[V], wq[V];
+        ld_pairs<W>(map, j << a.logTA, w, wq);
+#pragma unroll
+        for (int v = 0; v < V; ++v) x[j][v] = mul_twiddle<W, VAR>(x[j][v], w[v], wq[v], a.p);
+    }
+}
+
+// ------------------------------------------------------------ tile geometry
+
+// Column pass: CTA iteration `tile` covers sub-tiles tile*per_cta + ti, each
+// R rows x TV vectors of one block; 2^ltb sub-tiles per block, 2^lbt blocks
+// per transform.  Row pass: iteration `tile` covers rows tile*per_cta + r.
+template <typename W, int LOGR, bool ROW>
+struct Geo {
+    static constexpr int LOGS = ROW ? LOGR - Lanes<W>::LOGV : LOGR;  // vector-index bits
+    static constexpr uint32_t NS = 1u << LOGS;                       // vectors per sub-transform
+    static constexpr uint32_t NSP = NS + (NS >> 3);                  // with padding
+    using S = Sched<LOGS>;
+
+    int logTV, ltb, lbt;
+    uint32_t sub_total;  // column pass: sub-tiles in the pass
+
+    __device__ __forceinline__ explicit Geo(const PassArgs<W> &a) {
+        logTV = ROW ? 0 : a.logTV;
+        ltb = ROW ? 0 : a.logS - a.logTV - Lanes<W>::LOGV;
+        lbt = ROW ? 0 : a.logL - LOGR - a.logS;
+        sub_total = ROW ? 0 : (a.batch << (ltb + lbt));
+    }
+    // column pass: origin of sub-tile t, and its column-tile index ct
+    __device__ __forceinline__ W *col_origin(const PassArgs<W> &a, uint32_t t, uint32_t &ct) const {
+        ct = t & ((1u << ltb) - 1u);
+        const uint32_t blk = (t >> ltb) & ((1u << lbt) - 1u), b = t >> (ltb + lbt);
+        return a.data + (uint64_t)b * a.stride + ((uint64_t)blk << (LOGR + a.logS)) +
+               ((uint64_t)ct << (logTV + Lanes<W>::LOGV));
+    }
+    __device__ __forceinline__ W *row_ptr(const PassArgs<W> &a, uint64_t row) const {
+        if (a.rowptrs) return a.rowptrs[row];
+        const int shift = a.logL - LOGR;
+        const uint64_t b = row >> shift, within = row & ((1ull << shift) - 1ull);
+        return a.data + b * a.stride + (within << LOGR);
+    }
+};
+
+// Global <-> shared copies of one CTA iteration.  A load issues cp.async
+// copies (completed through commit/wait groups); a store reads shared memory
+// and writes 16-byte vectors.  Consecutive threads take consecutive 16-byte
+// chunks of a row, so both directions are coalesced.
+template <typename W, int LOGR, bool ROW, bool STORE>
+__device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOGR, ROW> &geo, uint32_t tile,
+                                          uint4 *buf) {
+    using G = Geo<W, LOGR, ROW>;
+    constexpr int V = Lanes<W>::V;
+    if (ROW) {
+        const uint64_t row0 = (uint64_t)tile * a.per_cta;
+        const uint32_t total = (uint32_t)a.per_cta << G::LOGS;
+        for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
+            const uint32_t q = i & (G::NS - 1), r = i >> G::LOGS;
+            const uint64_t row = row0 + r;
+            if (row >= a.nrows) continue;
+            W *g = geo.row_ptr(a, row) + q * V;
+            uint4 *s = buf + r * G::NSP + q + (q >> 3);
+            if (STORE)
+                *reinterpret_cast<uint4 *>(g) = *s;
+            else
+                cp_async16(s, g);
+        }
+    } else {
+        const int logTV = geo.logTV;
+        const uint32_t TV = 1u << logTV;
+        const uint64_t S = 1ull << a.logS;
+        const uint32_t total = (uint32_t)a.per_cta << (LOGR + logTV);
+        for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
+            const uint32_t cc = i & (TV - 1), s = (i >> logTV) & ((1u << LOGR) - 1u), ti = i >> (logTV + LOGR);
+            const uint32_t t = tile * a.per_cta + ti;
+            if (t >= geo.sub_total) continue;
+            uint32_t ct;
+            W *g = geo.col_origin(a, t, ct) + s * S + cc * V;
+            uint4 *sp = buf + ((ti * G::NSP + s + (s >> 3)) << logTV) + cc;
+            if (STORE)
+                *reinterpret_cast<uint4 *>(g) = *sp;
+            else
+                cp_async16(sp, g);
+        }
+    }
+}
+
+// One round over the tile in shared memory (compile-time round index RI).
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int RI>
+__device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LOGR, ROW> &geo, uint32_t tile,
+                                           uint4 *buf, const LaneTw<W> &lt) {
+    using G = Geo<W, LOGR, ROW>;
+    using S = typename G::S;
+    constexpr int V = Lanes<W>::V;
+    constexpr int LE = S::LE, E = S::E;
+    constexpr int B0 = S::b0(DIR, RI), NST = S::nst(DIR, RI);
+    constexpr bool FIRST = RI == 0, LAST = RI == S::NR - 1;
+    const W p = a.p, p2 = (W)(2 * a.p);
+    const int logTV = geo.logTV;
+    const uint32_t units = (uint32_t)a.per_cta << (G::LOGS - LE + logTV);
+    for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
+        const uint32_t tv = u & ((1u << logTV) - 1u);
+        const uint32_t g = (u >> logTV) & ((G::NS >> LE) - 1u);
+        const uint32_t ti = u >> (logTV + G::LOGS - LE);
+        const uint32_t lo = g & ((1u << B0) - 1u);
+        const uint32_t s0 = ((g >> B0) << (B0 + LE)) | lo;
+        uint4 *rp = buf + ((ti * G::NSP + s0 + (s0 >> 3)) << logTV) + tv;
+        W x[E][V];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
+            unpack(rp[cj << logTV], x[j]);
+        }
+        const bool mid = !ROW && (a.flags & F_MIDDLE) && ((DIR == DIR_INV && FIRST) || (DIR == DIR_FWD && LAST));
+        uint32_t c0 = 0;
+        if (mid) {
+            uint32_t ct;
+            geo.col_origin(a, tile * a.per_cta + ti, ct);
+            c0 = ((ct << logTV) + tv) * V;
+        }
+        if (DIR == DIR_INV && FIRST) {
+            if (mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+            if (ROW) lane_stages<W, DIR, VAR, E>(x, lt, p, p2);
+        }
+        const W *twp = a.tw + 2 * (ROW ? (lo << Lanes<W>::LOGV) : lo);
+        round_regs<W, DIR, VAR, LE, B0, NST, ROW>(x, twp, p, p2);
+        if (DIR == DIR_FWD && LAST) {
+            if (ROW) lane_stages<W, DIR, VAR, E>(x, lt, p, p2);
+            if (mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+        }
+        if (LAST && (a.flags & F_NORMALIZE)) normalize<W, DIR, VAR, E>(x, p, p2);
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
+            rp[cj << logTV] = pack<W>(x[j]);
+        }
+    }
+}
+
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int RI = 0>
+__device__ __forceinline__ void tile_rounds(const PassArgs<W> &a, const Geo<W, LOGR, ROW> &geo, uint32_t tile,
+                                            uint4 *buf, const LaneTw<W> &lt) {
+    tile_round<W, DIR, VAR, LOGR, ROW, RI>(a, geo, tile, buf, lt);
+    if constexpr (RI + 1 < Geo<W, LOGR, ROW>::S::NR) {
+        __syncthreads();
+        tile_rounds<W, DIR, VAR, LOGR, ROW, RI + 1>(a, geo, tile, buf, lt);
+    }
+}
+
+template <typename W>
+__device__ __forceinline__ LaneTw<W> load_lane_tw(const W *tw) {
+    LaneTw<W> lt;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ld_pair(tw, 1 + i, lt.w[i], lt.wq[i]);
+    return lt;
+}
+
+// One CTA iteration without pipelining (used by the persistent uneven-batch
+// kernel, whose next item may depend on this one).
+template <typename W, int DIR, int VAR, int LOGR, bool ROW>
+__device__ __forceinline__ void process_tile(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
+    const Geo<W, LOGR, ROW> geo(a);
+    const LaneTw<W> lt = load_lane_tw(a.tw);
+    tile_copy<W, LOGR, ROW, false>(a, geo, tile, buf);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    tile_rounds<W, DIR, VAR, LOGR, ROW>(a, geo, tile, buf, lt);
+    __syncthreads();
+    tile_copy<W, LOGR, ROW, true>(a, geo, tile, buf);
+    __syncthreads();
+}
+
+// One pass over a batch: persistent CTAs with cp.async double buffering.
+template <typename W, int DIR, int VAR, int LOGR, bool ROW>
 __global__ void __launch_bounds__(kThreads) k_pass(const PassArgs<W> a) {
     extern __shared__ uint4 sm[];
-    pass_cta<W, DIR, VAR, ROW, false>(a, blockIdx.x, sm);
+    const Geo<W, LOGR, ROW> geo(a);
+    const LaneTw<W> lt = load_lane_tw(a.tw);
+    uint32_t tile = blockIdx.x;
+    if (tile < a.ntiles) tile_copy<W, LOGR, ROW, false>(a, geo, tile, sm);
+    cp_async_commit();
+    for (uint32_t it = 0; tile < a.ntiles; tile += gridDim.x, ++it) {
+        uint4 *cur = (it & 1) ? sm + a.buf_chunks : sm;
+        uint4 *nxt = (it & 1) ? sm : sm + a.buf_chunks;
+        const uint32_t next = tile + gridDim.x;
+        if (next < a.ntiles) tile_copy<W, LOGR, ROW, false>(a, geo, next, nxt);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        tile_rounds<W, DIR, VAR, LOGR, ROW>(a, geo, tile, cur, lt);
+        __syncthreads();
+        tile_copy<W, LOGR, ROW, true>(a, geo, tile, cur);
+        __syncthreads();
+    }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------------------
@@ -425,22 +505,16 @@ __global__ void k_tiny(const PassArgs<W> a) {
             for (int t = 0; t < L; t += 2 * m)
                 for (int k = 0; k < m; ++k) {
                     W w, wq;
-                    load_pair(a.tw, m - 1 + k, w, wq);
-                    if (VAR == VAR_LAZY)
-                        bfly_fwd_lazy(x[t + k], x[t + k + m], w, wq, p, p2);
-                    else
-                        bfly_fwd_ntl(x[t + k], x[t + k + m], w, wq, p);
+                    ld_pair(a.tw, m + k, w, wq);
+                    bfly<W, DIR, VAR>(x[t + k], x[t + k + m], w, wq, p, p2);
                 }
     } else {
         for (int m = 1; m < L; m <<= 1)
             for (int t = 0; t < L; t += 2 * m)
                 for (int k = 0; k < m; ++k) {
                     W w, wq;
-                    load_pair(a.tw, m - 1 + k, w, wq);
-                    if (VAR == VAR_LAZY)
-                        bfly_inv_lazy(x[t + k], x[t + k + m], w, wq, p, p2);
-                    else
-                        bfly_inv_ntl(x[t + k], x[t + k + m], w, wq, p);
+                    ld_pair(a.tw, m + k, w, wq);
+                    bfly<W, DIR, VAR>(x[t + k], x[t + k + m], w, wq, p, p2);
                 }
     }
     for (int i = 0; i < L; ++i) {

@@ -3,6 +3,8 @@
 // word types compile in parallel.
 #pragma once
 
+#include <algorithm>
+
 #include "ntt_internal.hpp"
 #include "ntt_kernels.cuh"
 
@@ -15,11 +17,12 @@ static PassArgs<W> to_args(const LaunchSpec &s) {
     a.stride = s.stride;
     a.batch = s.batch;
     a.logL = s.logL;
-    a.logR = s.logR;
     a.logS = s.logS;
-    a.per_cta = s.per_cta;
     a.logTV = s.logTV;
     a.logTA = s.logTA;
+    a.per_cta = s.per_cta;
+    a.ntiles = s.ntiles;
+    a.buf_chunks = s.buf_chunks;
     a.flags = s.flags;
     a.tw = static_cast<const W *>(s.tw);
     a.ma = static_cast<const W *>(s.ma);
@@ -30,31 +33,68 @@ static PassArgs<W> to_args(const LaunchSpec &s) {
     return a;
 }
 
-template <typename W, int DIR, int VAR, bool ROW>
-static cudaError_t launch_one(const LaunchSpec &s, cudaStream_t st) {
-    auto kern = k_pass<W, DIR, VAR, ROW>;
-    // Opt in to large dynamic shared memory once per device and kernel.
+// Per kernel: shared-memory opt-in once per device, and the number of CTAs
+// that fit on one SM for the launch's shared-memory size (cached).  The
+// caches are per kernel instantiation (template arguments), not per
+// function type, which every k_pass of one word type shares.
+template <typename W, int DIR, int VAR, int LOGR, bool ROW>
+static cudaError_t kernel_slots(size_t smem, int *per_sm, int *sms) {
+    auto kern = k_pass<W, DIR, VAR, LOGR, ROW>;
     static int configured[64] = {0};
+    static int cache_occ[64], cache_sms[64];
+    static size_t cache_smem[64];
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !configured[dev]) {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+        e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
+        cudaDeviceGetAttribute(&cache_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        cache_smem[dev] = (size_t)-1;
         configured[dev] = 1;
     }
-    kern<<<s.grid, kThreads, s.smem, st>>>(to_args<W>(s));
+    if (cache_smem[dev] != smem) {
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        cache_occ[dev] = std::max(occ, 1);
+        cache_smem[dev] = smem;
+    }
+    *per_sm = cache_occ[dev];
+    *sms = cache_sms[dev];
+    return cudaSuccess;
+}
+
+// Persistent grid: no more CTAs than fit on the device at once.
+template <typename W, int DIR, int VAR, int LOGR, bool ROW>
+static cudaError_t launch_k(const LaunchSpec &s, cudaStream_t st) {
+    auto kern = k_pass<W, DIR, VAR, LOGR, ROW>;
+    int per_sm = 1, sms = 1;
+    cudaError_t e = kernel_slots<W, DIR, VAR, LOGR, ROW>(s.smem, &per_sm, &sms);
+    if (e != cudaSuccess) return e;
+    const uint64_t slots = (uint64_t)per_sm * sms;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(s.ntiles, slots));
+    kern<<<grid, kThreads, s.smem, st>>>(to_args<W>(s));
     return cudaGetLastError();
+}
+
+template <typename W, int DIR, int VAR, bool ROW, int LO, int HI>
+static cudaError_t launch_logr(const LaunchSpec &s, int logR, cudaStream_t st) {
+    if (logR == LO) return launch_k<W, DIR, VAR, LO, ROW>(s, st);
+    if constexpr (LO < HI) return launch_logr<W, DIR, VAR, ROW, LO + 1, HI>(s, logR, st);
+    return cudaErrorInvalidValue;
 }
 
 template <typename W, int DIR, int VAR>
 static cudaError_t launch_kind(const LaunchSpec &s, int kind, cudaStream_t st) {
-    if (kind == 0) return launch_one<W, DIR, VAR, false>(s, st);
-    if (kind == 1) return launch_one<W, DIR, VAR, true>(s, st);
+    if (kind == 0) return launch_logr<W, DIR, VAR, false, 3, kMaxColLog>(s, s.logR, st);
+    if (kind == 1) return launch_logr<W, DIR, VAR, true, 3, kMaxRowLog>(s, s.logR, st);
     k_tiny<W, DIR, VAR><<<s.grid, 128, 0, st>>>(to_args<W>(s));
     return cudaGetLastError();
 }

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ntt_internal.hpp"
+#include "ntt_kernels.cuh"
 
 namespace ntt {
 
@@ -178,12 +179,14 @@ static int build_tables(ntt_plan_s *pl) {
     const int logV = pl->wbytes == 4 ? 2 : 1;
     int maxr = 0;
     for (int q = 0; q < pl->npass; ++q) maxr = std::max(maxr, pl->pass[q].logR);
-    pl->tw_log = std::max(1, maxr);
+    pl->tw_log = std::max(2, maxr);  // lane stages read entries 1..3
     for (int d = 0; d < 2; ++d) {
         const uint64_t root = d == 0 ? pl->omega : pl->omega_inv;
-        // stage table: entry m-1+k = root^(k L / 2m), for m = 1, 2, ..., 2^(tw_log-1)
+        // stage table: entry m+k = root^(k L / 2m), for m = 1, 2, ..., 2^(tw_log-1);
+        // entry 0 is unused (set to W = 1)
         std::vector<uint64_t> tw;
         tw.reserve(2 * ((size_t)1 << pl->tw_log));
+        push_pair(tw, 1, p, bits);
         for (int b = 0; b < pl->tw_log; ++b) {
             const uint64_t m = 1ull << b;
             const uint64_t step = nt::powmod(root, pl->L / (2 * m), p);
@@ -193,6 +196,7 @@ static int build_tables(ntt_plan_s *pl) {
                 w = nt::mulmod(w, step, p);
             }
         }
+        tw.resize(2 * ((size_t)1 << pl->tw_log));  // 2^tw_log entries: [0] + m in [1, 2^tw_log)
         int rc = upload_pairs(pl, tw, &pl->tw[d]);
         if (rc) return rc;
         // middle tables of the column passes
@@ -269,7 +273,6 @@ int enqueue_transform(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t 
 
 int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stride, cudaStream_t st, int first,
                   int count) {
-    const int logV = pl->wbytes == 4 ? 2 : 1;
     LaunchSpec s;
     memset(&s, 0, sizeof(s));
     s.data = data;
@@ -289,44 +292,50 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
         const PassPlan &ps = pl->pass[q];
         s.logR = ps.logR;
         s.logS = ps.logS;
-        s.flags = 0;
-        const bool last_exec = (i == n - 1);
-        if (last_exec) s.flags |= 1;  // F_NORMALIZE
-        const uint32_t R = 1u << ps.logR;
-        int kind;
-        if (q == n - 1) {  // row pass
-            kind = 1;
-            s.logTV = 0;
-            s.per_cta = (int)std::max<uint32_t>(1, 2048u / R);
-            s.nrows = (uint64_t)batch << (pl->logL - ps.logR);
-            const uint64_t rows_per_cta = (uint64_t)s.per_cta << logV;
-            s.grid = (unsigned)((s.nrows + rows_per_cta - 1) / rows_per_cta);
-            s.smem = (size_t)s.per_cta * R * 16;
-            s.ma = s.mb = nullptr;
-        } else {
-            kind = 0;
-            // Narrower tiles (down to 32-byte rows) when 128-byte rows would
-            // leave fewer than two CTAs per SM.
-            int logTV = ps.logTV;
-            while (logTV > 1 && ((uint64_t)batch << (pl->logL - ps.logR - logTV - logV)) < 2 * 152) --logTV;
-            s.logTV = logTV;
+        s.flags = (i == n - 1) ? 1 : 0;  // F_NORMALIZE on the last executed pass
+        tile_params(pl, q, batch, s);
+        const int kind = q == n - 1 ? 1 : 0;
+        if (kind == 0) {
             s.logTA = ps.logTA;
             s.flags |= 2 | (ps.has_mb ? 4 : 0);  // F_MIDDLE, F_MB
             s.ma = ps.ma[dir];
             s.mb = ps.mb[dir];
-            const uint32_t tile_chunks = R << logTV;
-            const uint32_t tile_units = tile_chunks >> 3;
-            s.per_cta = (int)std::max<uint32_t>(1, 256u / std::max<uint32_t>(tile_units, 1));
-            while ((size_t)s.per_cta * tile_chunks * 16 > 64 * 1024 && s.per_cta > 1) s.per_cta >>= 1;
-            const uint64_t tiles = (uint64_t)batch << (pl->logL - ps.logR - logTV - logV);
-            s.grid = (unsigned)((tiles + s.per_cta - 1) / s.per_cta);
-            s.smem = (size_t)s.per_cta * tile_chunks * 16;
-            s.nrows = 0;
+        } else {
+            s.ma = s.mb = nullptr;
         }
+        s.smem = (size_t)2 * s.buf_chunks * 16;  // double buffer
         cudaError_t e = launch(pl, s, kind, dir, st);
         if (e != cudaSuccess) return cuda_fail(e, "launch pass");
     }
     return NTT_OK;
+}
+
+void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s) {
+    const PassPlan &ps = pl->pass[q];
+    const int logV = pl->wbytes == 4 ? 2 : 1;
+    const int logR = ps.logR;
+    if (q == pl->npass - 1) {  // row pass: vectors of V consecutive elements
+        const int logS = logR - logV;
+        const int le = std::min(3, logS);
+        const uint32_t units_per_row = 1u << (logS - le);
+        const uint32_t ns = 1u << logS, nsp = ns + (ns >> 3);
+        s.logTV = 0;
+        s.per_cta = (int)std::max<uint32_t>(1, kThreads / units_per_row);
+        s.nrows = s.nrows ? s.nrows : (batch << (pl->logL - logR));
+        s.ntiles = (uint32_t)((s.nrows + s.per_cta - 1) / s.per_cta);
+        s.buf_chunks = (uint32_t)s.per_cta * nsp;
+    } else {  // column pass: R rows x TV vectors per sub-tile
+        int logTV = std::min(ps.logTV, std::max(0, 11 - logR));  // R * TV <= 2048 vectors per buffer
+        while (logTV > 1 && (batch << (pl->logL - logR - logTV - logV)) < 4 * 152) --logTV;
+        const uint32_t units = (1u << (logR + logTV)) >> 3;
+        const uint32_t nsp = (1u << logR) + (1u << logR >> 3);
+        s.logTV = logTV;
+        s.per_cta = (int)std::max<uint32_t>(1, kThreads / units);
+        const uint64_t sub = batch << (pl->logL - logR - logTV - logV);
+        s.ntiles = (uint32_t)((sub + s.per_cta - 1) / s.per_cta);
+        s.buf_chunks = ((uint32_t)s.per_cta * nsp) << logTV;
+        s.nrows = 0;
+    }
 }
 
 }  // namespace ntt

@@ -36,7 +36,8 @@ namespace ntt {
 
 struct UStage {
     const uint32_t *ma, *mb;
-    uint32_t units;  // CTAs-worth of work (items) in this stage
+    uint32_t units;  // CTA iterations (work items) of this stage
+    uint32_t buf_chunks;
     int8_t logR, logS, logTV, logTA, row;
     uint8_t flags;
     uint16_t per_cta;
@@ -74,18 +75,28 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile const int *)p; }
 
+template <int DIR, bool ROW, int LO, int HI>
+__device__ __forceinline__ void run_logr(int logR, const PassArgs<uint32_t> &a, uint32_t tile, uint4 *sm) {
+    if (logR == LO) {
+        process_tile<uint32_t, DIR, VAR_LAZY, LO, ROW>(a, tile, sm);
+        return;
+    }
+    if constexpr (LO < HI) run_logr<DIR, ROW, LO + 1, HI>(logR, a, tile, sm);
+}
+
 template <int DIR, bool ROW>
 __device__ __forceinline__ void run_item(const UTask &t, const UStage &sg, uint32_t cta, uint4 *sm) {
     PassArgs<uint32_t> a;
     a.data = t.data;
-    a.stride = 1u << t.logL;
+    a.stride = 1ull << t.logL;
     a.batch = 1;
     a.logL = t.logL;
-    a.logR = sg.logR;
     a.logS = sg.logS;
-    a.per_cta = sg.per_cta;
     a.logTV = sg.logTV;
     a.logTA = sg.logTA;
+    a.per_cta = sg.per_cta;
+    a.ntiles = sg.units;
+    a.buf_chunks = sg.buf_chunks;
     a.flags = sg.flags;
     a.tw = t.tw;
     a.ma = sg.ma;
@@ -93,7 +104,10 @@ __device__ __forceinline__ void run_item(const UTask &t, const UStage &sg, uint3
     a.p = t.p;
     a.rowptrs = t.rowptrs;
     a.nrows = t.rowptrs ? t.nrows : (1ull << (t.logL - sg.logR));
-    pass_cta<uint32_t, DIR, VAR_LAZY, ROW, true>(a, cta, sm);
+    if (ROW)
+        run_logr<DIR, true, 3, kMaxRowLog>(sg.logR, a, cta, sm);
+    else
+        run_logr<DIR, false, 3, kMaxColLog>(sg.logR, a, cta, sm);
 }
 
 __global__ void __launch_bounds__(kThreads) k_uneven(const UTask *__restrict__ tasks, const UItem *__restrict__ items,
@@ -198,35 +212,27 @@ static UStage make_stage(const ntt_plan_s *pl, int dir, int i, uint32_t nrows_cl
     const int n = pl->npass;
     const int q = dir == 0 ? i : n - 1 - i;
     const PassPlan &ps = pl->pass[q];
+    LaunchSpec s;
+    memset(&s, 0, sizeof(s));
+    s.nrows = nrows_class;
+    tile_params(pl, q, 1, s);
     UStage sg;
     memset(&sg, 0, sizeof(sg));
     sg.logR = (int8_t)ps.logR;
     sg.logS = (int8_t)ps.logS;
     sg.flags = (i == n - 1) ? F_NORMALIZE : 0;
-    const uint32_t R = 1u << ps.logR;
-    if (q == n - 1) {
-        sg.row = 1;
-        sg.logTV = 0;
-        sg.per_cta = (uint16_t)std::max<uint32_t>(1, 2048u / R);
-        const uint64_t nrows = nrows_class ? nrows_class : (1ull << (pl->logL - ps.logR));
-        const uint64_t per = (uint64_t)sg.per_cta * 4;
-        sg.units = (uint32_t)((nrows + per - 1) / per);
-        *smem = std::max(*smem, (size_t)sg.per_cta * R * 16);
-    } else {
-        sg.row = 0;
-        sg.logTV = (int8_t)ps.logTV;
+    sg.row = q == n - 1 ? 1 : 0;
+    sg.logTV = (int8_t)s.logTV;
+    sg.per_cta = (uint16_t)s.per_cta;
+    sg.units = s.ntiles;
+    sg.buf_chunks = s.buf_chunks;
+    if (!sg.row) {
         sg.logTA = (int8_t)ps.logTA;
         sg.flags |= F_MIDDLE | (ps.has_mb ? F_MB : 0);
         sg.ma = (const uint32_t *)ps.ma[dir];
         sg.mb = (const uint32_t *)ps.mb[dir];
-        const uint32_t tile_chunks = R << ps.logTV;
-        uint32_t per = std::max<uint32_t>(1, 256u / std::max<uint32_t>(tile_chunks >> 3, 1));
-        while ((size_t)per * tile_chunks * 16 > 64 * 1024 && per > 1) per >>= 1;
-        sg.per_cta = (uint16_t)per;
-        const uint64_t tiles = 1ull << (pl->logL - ps.logR - ps.logTV - 2);
-        sg.units = (uint32_t)((tiles + per - 1) / per);
-        *smem = std::max(*smem, (size_t)per * tile_chunks * 16);
     }
+    *smem = std::max(*smem, (size_t)s.buf_chunks * 16);
     return sg;
 }
 
