@@ -109,6 +109,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def alu_peak_bfly(word_bytes, sm_mhz):
+    """Integer-multiply roof in butterflies/s: per SM and clock, 32 mul.hi and
+    64 mad.lo (measured rates of this GB300), 1 + 2 of them per 32-bit lazy
+    butterfly (Section 5: three multiplies) -> 16 butterflies/clk/SM.  A
+    64-bit butterfly needs about 4x the 32-bit multiply work."""
+    per_clk = 16.0 if word_bytes == 4 else 4.0
+    return 152 * sm_mhz * 1e6 * per_clk
+
+
 def butterflies(groups):
     """Butterflies per forward (or inverse) transform set: l * L/2 per vector (Section 5 count)."""
     return sum(b * l * (1 << l) // 2 for (_, l, b) in groups)
@@ -185,10 +194,27 @@ def barrier(dist):
         dist.barrier()
 
 
-def time_steps(wl, torch, K, W, dist, with_events=False):
+def capture_step(wl, torch):
+    """CUDA graph of one step (forward + inverse of every group on its own
+    stream, forked from and joined back to the capturing stream)."""
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            wl.step()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    return g
+
+
+def time_steps(wl, torch, K, W, dist, graph=None, with_events=False):
+    """K timed steps (graph replays when a graph is given), L2 flushed before
+    each; returns (total ms of the K steps, per-pass events, wall window)."""
+    run = (lambda ev=None: graph.replay()) if graph is not None else (lambda ev=None: wl.step(ev))
     for _ in range(W):
         wl.flush_l2()
-        wl.step()
+        run()
     torch.cuda.synchronize()
     barrier(dist)
     torch.cuda.synchronize()
@@ -199,7 +225,7 @@ def time_steps(wl, torch, K, W, dist, with_events=False):
         wl.flush_l2()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
-        wl.step(events if with_events else None)
+        run(events if with_events else None)
         s1.record()
         per_step.append((s0, s1))
     torch.cuda.synchronize()
@@ -296,27 +322,56 @@ def run_ours(args, dist, rank, world):
     bfly_step = 2 * butterflies(groups)
     bytes_step = 2 * useful_bytes(groups)
 
+    # headline: graph replays of the whole step (lazy butterflies)
     wl.set_variant(0)
-    ms_lazy, events, (t0, t1) = time_steps(wl, torch, args.steps, args.warmup, dist, with_events=True)
+    for _ in range(3):
+        wl.step()
+    torch.cuda.synchronize()
+    graph = capture_step(wl, torch)
+    ms_lazy, _, (t0, t1) = time_steps(wl, torch, args.steps, args.warmup, dist, graph=graph)
     clocks = sampler.stop(t0, t1)
     ms_lazy = max_over_ranks(ms_lazy, dist, torch)
+    # per-kernel durations: the same step launched eagerly, CUDA events around each pass
+    _, events, _ = time_steps(wl, torch, args.steps, args.warmup, dist, with_events=True)
     stats, dom = kernel_stats(events, groups)
+    # comparator: Algorithm 2 butterflies in the same schedule
     wl.set_variant(1)
-    ms_ntl, _, _ = time_steps(wl, torch, args.steps, args.warmup, dist)
+    for _ in range(3):
+        wl.step()
+    graph_ntl = capture_step(wl, torch)
+    ms_ntl, _, _ = time_steps(wl, torch, args.steps, args.warmup, dist, graph=graph_ntl)
     ms_ntl = max_over_ranks(ms_ntl, dist, torch)
     wl.set_variant(0)
-    ms_e2e = time_e2e(wl, torch, max(3, min(args.steps, 50)), 2, dist)
     k_e2e = max(3, min(args.steps, 50))
+    ms_e2e = time_e2e(wl, torch, k_e2e, 2, dist)
     ms_e2e = max_over_ranks(ms_e2e, dist, torch)
 
     K = args.steps
     value = world * bfly_step * K / (ms_lazy / 1e3)
     ntl_value = world * bfly_step * K / (ms_ntl / 1e3)
     ds = stats[dom]
-    achieved = ds["bytes"] / (ds["avg_ms"] / 1e3) / 1e9
     gi, inv, k = dom
     p_, l_, b_ = groups[gi]
-    dom_name = f"{'inverse' if inv else 'forward'} pass {k} of {b_} x 2^{l_}"
+    w_ = 4 if p_ < (1 << 30) else 8
+    achieved_gbs = ds["bytes"] / (ds["avg_ms"] / 1e3) / 1e9
+    # butterflies of the dominant pass: every element takes log2(R) / 2 of them
+    log_r = wl.plans[gi].info().log_r[k if not inv else wl.nsteps[gi] - 1 - k]
+    pass_bfly = b_ * (1 << l_) * log_r / 2
+    achieved_bfly = pass_bfly / (ds["avg_ms"] / 1e3)
+    alu_peak = alu_peak_bfly(w_, peaks["sm_max_mhz"])
+    frac_hbm = achieved_gbs / peaks["hbm_gbs"]
+    frac_alu = achieved_bfly / alu_peak
+    dom_name = f"{'inverse' if inv else 'forward'} pass {k} of {b_} x 2^{l_} (log2 R = {log_r})"
+    if frac_alu >= frac_hbm:
+        roof = {"bound": "alu", "achieved": achieved_bfly / 1e9, "peak": alu_peak / 1e9, "unit": "Gbutterflies/s",
+                "frac": frac_alu, "traffic": None, "kernel": dom_name,
+                "peak_src": "152 SMs x clock x 16 lazy butterflies/clk/SM (integer-multiply pipe)",
+                "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": frac_hbm}}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": frac_hbm, "traffic": None, "kernel": dom_name, "peak_src": peaks["src"] + " (MEASURED_PEAKS.json)",
+                "alu": {"achieved": achieved_bfly / 1e9, "peak": alu_peak / 1e9, "unit": "Gbutterflies/s",
+                        "frac": frac_alu}}
     line = {
         "metric": METRIC,
         "value": value,
@@ -335,13 +390,12 @@ def run_ours(args, dist, rank, world):
         "hbm_gbs_useful": world * bytes_step * K / (ms_lazy / 1e3) / 1e9,
         "ntl": {"value": ntl_value, "unit": "butterflies/s", "ms_per_step": ms_ntl / K},
         "lazy_over_ntl": ms_ntl / ms_lazy,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": dom_name, "peak_src": peaks["src"]},
+        "roofline": roof,
         "kernels": {f"g{g}{'i' if i else 'f'}{s}": round(v["avg_ms"] * 1e3, 2) for (g, i, s), v in stats.items()},
         "e2e": {"value": world * bfly_step * k_e2e / (ms_e2e / 1e3), "unit": "butterflies/s",
                 "h2d_bytes_per_step": useful_bytes(groups) // 2, "d2h_bytes_per_step": useful_bytes(groups) // 2},
         "gpu_launches": len(events) // K,
+        "graph": "timed steps are CUDA graph replays; kernel times from an eager pass with events",
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

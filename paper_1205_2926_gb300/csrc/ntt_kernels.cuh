@@ -309,6 +309,13 @@ struct Geo {
     static constexpr uint32_t NS = 1u << LOGS;                       // vectors per sub-transform
     static constexpr uint32_t NSP = NS + (NS >> 3);                  // with padding
     using S = Sched<LOGS>;
+    // The last round stores straight from registers when its vectors are
+    // contiguous across neighbouring threads: always for a column pass, and
+    // for the inverse row pass once eight neighbouring threads hold
+    // neighbouring vectors (b0 >= 3).
+    __host__ __device__ static constexpr bool DIRECT_STORE(int dir) {
+        return !ROW || (dir == DIR_INV && S::b0(DIR_INV, S::NR - 1) >= 3);
+    }
 
     int logTV, ltb, lbt;
     uint32_t sub_total;  // column pass: sub-tiles in the pass
@@ -337,7 +344,8 @@ struct Geo {
 // Global <-> shared copies of one CTA iteration.  A load issues cp.async
 // copies (completed through commit/wait groups); a store reads shared memory
 // and writes 16-byte vectors.  Consecutive threads take consecutive 16-byte
-// chunks of a row, so both directions are coalesced.
+// chunks of a row, so both directions are coalesced; addresses advance by
+// constant strides from a per-thread base.
 template <typename W, int LOGR, bool ROW, bool STORE>
 __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOGR, ROW> &geo, uint32_t tile,
                                           uint4 *buf) {
@@ -345,34 +353,61 @@ __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOG
     constexpr int V = Lanes<W>::V;
     if (ROW) {
         const uint64_t row0 = (uint64_t)tile * a.per_cta;
-        const uint32_t total = (uint32_t)a.per_cta << G::LOGS;
-        for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
-            const uint32_t q = i & (G::NS - 1), r = i >> G::LOGS;
-            const uint64_t row = row0 + r;
-            if (row >= a.nrows) continue;
-            W *g = geo.row_ptr(a, row) + q * V;
-            uint4 *s = buf + r * G::NSP + q + (q >> 3);
-            if (STORE)
-                *reinterpret_cast<uint4 *>(g) = *s;
-            else
-                cp_async16(s, g);
+        if (G::NS >= (uint32_t)kThreads) {
+            // whole rows, kThreads chunks per step
+            for (int r = 0; r < a.per_cta; ++r) {
+                if (row0 + r >= a.nrows) break;
+                W *g = geo.row_ptr(a, row0 + r) + threadIdx.x * V;
+                uint4 *sp = buf + r * G::NSP + threadIdx.x + (threadIdx.x >> 3);
+#pragma unroll 4
+                for (uint32_t q = threadIdx.x; q < G::NS; q += kThreads) {
+                    if (STORE)
+                        *reinterpret_cast<uint4 *>(g) = *sp;
+                    else
+                        cp_async16(sp, g);
+                    g += kThreads * V;
+                    sp += kThreads + kThreads / 8;
+                }
+            }
+        } else {
+            // several rows per step: chunk q of row r
+            constexpr uint32_t rows_step = kThreads >> G::LOGS;
+            const uint32_t q = threadIdx.x & (G::NS - 1);
+            uint4 *sp = buf + (threadIdx.x >> G::LOGS) * G::NSP + q + (q >> 3);
+            for (uint32_t r = threadIdx.x >> G::LOGS; r < (uint32_t)a.per_cta; r += rows_step) {
+                if (row0 + r < a.nrows) {
+                    W *g = geo.row_ptr(a, row0 + r) + q * V;
+                    if (STORE)
+                        *reinterpret_cast<uint4 *>(g) = *sp;
+                    else
+                        cp_async16(sp, g);
+                }
+                sp += rows_step * G::NSP;
+            }
         }
     } else {
         const int logTV = geo.logTV;
-        const uint32_t TV = 1u << logTV;
+        const uint32_t cc = threadIdx.x & ((1u << logTV) - 1u);
+        const uint32_t rows_step = (uint32_t)kThreads >> logTV;  // >= 32, a multiple of 8
         const uint64_t S = 1ull << a.logS;
-        const uint32_t total = (uint32_t)a.per_cta << (LOGR + logTV);
-        for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
-            const uint32_t cc = i & (TV - 1), s = (i >> logTV) & ((1u << LOGR) - 1u), ti = i >> (logTV + LOGR);
+        for (uint32_t srow = threadIdx.x >> logTV; srow < ((uint32_t)a.per_cta << LOGR);) {
+            const uint32_t ti = srow >> LOGR;
             const uint32_t t = tile * a.per_cta + ti;
-            if (t >= geo.sub_total) continue;
+            if (t >= geo.sub_total) break;
             uint32_t ct;
+            uint32_t s = srow & ((1u << LOGR) - 1u);
             W *g = geo.col_origin(a, t, ct) + s * S + cc * V;
             uint4 *sp = buf + ((ti * G::NSP + s + (s >> 3)) << logTV) + cc;
-            if (STORE)
-                *reinterpret_cast<uint4 *>(g) = *sp;
-            else
-                cp_async16(sp, g);
+            const uint64_t gstep = rows_step * S;
+            const uint32_t sstep = (rows_step + rows_step / 8) << logTV;
+            for (; s < (1u << LOGR); s += rows_step, srow += rows_step) {
+                if (STORE)
+                    *reinterpret_cast<uint4 *>(g) = *sp;
+                else
+                    cp_async16(sp, g);
+                g += gstep;
+                sp += sstep;
+            }
         }
     }
 }
@@ -421,10 +456,32 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
             if (mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
         }
         if (LAST && (a.flags & F_NORMALIZE)) normalize<W, DIR, VAR, E>(x, p, p2);
+        if (LAST && G::DIRECT_STORE(DIR)) {
+            // last round writes straight to HBM (coalesced for this layout)
+            if (ROW) {
+                const uint64_t row = (uint64_t)tile * a.per_cta + ti;
+                if (row < a.nrows) {
+                    W *gp = geo.row_ptr(a, row) + s0 * V;
 #pragma unroll
-        for (int j = 0; j < E; ++j) {
-            const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
-            rp[cj << logTV] = pack<W>(x[j]);
+                    for (int j = 0; j < E; ++j) *reinterpret_cast<uint4 *>(gp + ((j << B0) * V)) = pack<W>(x[j]);
+                }
+            } else {
+                const uint32_t t = tile * a.per_cta + ti;
+                if (t < geo.sub_total) {
+                    uint32_t ct;
+                    const uint64_t S = 1ull << a.logS;
+                    W *gp = geo.col_origin(a, t, ct) + s0 * S + tv * V;
+#pragma unroll
+                    for (int j = 0; j < E; ++j)
+                        *reinterpret_cast<uint4 *>(gp + (uint64_t)(j << B0) * S) = pack<W>(x[j]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
+                rp[cj << logTV] = pack<W>(x[j]);
+            }
         }
     }
 }
@@ -459,13 +516,15 @@ __device__ __forceinline__ void process_tile(const PassArgs<W> &a, uint32_t tile
     __syncthreads();
     tile_rounds<W, DIR, VAR, LOGR, ROW>(a, geo, tile, buf, lt);
     __syncthreads();
-    tile_copy<W, LOGR, ROW, true>(a, geo, tile, buf);
-    __syncthreads();
+    if (!Geo<W, LOGR, ROW>::DIRECT_STORE(DIR)) {
+        tile_copy<W, LOGR, ROW, true>(a, geo, tile, buf);
+        __syncthreads();
+    }
 }
 
 // One pass over a batch: persistent CTAs with cp.async double buffering.
 template <typename W, int DIR, int VAR, int LOGR, bool ROW>
-__global__ void __launch_bounds__(kThreads) k_pass(const PassArgs<W> a) {
+__global__ void __launch_bounds__(kThreads, ROW ? 2 : 3) k_pass(const PassArgs<W> a) {
     extern __shared__ uint4 sm[];
     const Geo<W, LOGR, ROW> geo(a);
     const LaneTw<W> lt = load_lane_tw(a.tw);
@@ -482,8 +541,10 @@ __global__ void __launch_bounds__(kThreads) k_pass(const PassArgs<W> a) {
         __syncthreads();
         tile_rounds<W, DIR, VAR, LOGR, ROW>(a, geo, tile, cur, lt);
         __syncthreads();
-        tile_copy<W, LOGR, ROW, true>(a, geo, tile, cur);
-        __syncthreads();
+        if (!Geo<W, LOGR, ROW>::DIRECT_STORE(DIR)) {
+            tile_copy<W, LOGR, ROW, true>(a, geo, tile, cur);
+            __syncthreads();
+        }
     }
     cp_async_wait<0>();
 }

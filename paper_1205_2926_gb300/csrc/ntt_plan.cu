@@ -252,7 +252,11 @@ static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
         if (q < n - 1) {
             ps.logTV = max_logtv(ps.logS, pl->wbytes);
             const int logT = ps.logTV + logV;
-            ps.logTA = std::min(ps.logS, std::max(logT, (ps.logS + 1) / 2));
+            // One middle-twiddle table MA of B pairs (a single Shoup product per
+            // element) while it stays small enough to live in L2 (<= 2 MiB);
+            // beyond that MA and MB of about 2 R sqrt(S) pairs.
+            const bool full = ((uint64_t)2 * pl->wbytes << (ps.logR + ps.logS)) <= (2u << 20);
+            ps.logTA = full ? ps.logS : std::min(ps.logS, std::max(logT, (ps.logS + 1) / 2));
             ps.has_mb = ps.logTA < ps.logS;
         }
         logB -= logr[q];
