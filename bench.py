@@ -43,6 +43,11 @@ WORKLOADS = {
            "groups": [(P_NTT30, 16, 64), (P_NTT30, 20, 1), (P_NTT30, 22, 1)]},
     "c3": {"name": "64-bit NTT, p=2305843009448574977: 16 x 2^20 + 1 x 2^24, forward+inverse",
            "groups": [(P_NTT62, 20, 16), (P_NTT62, 24, 1)]},
+    "c4": {"name": "uneven batch: 4096 transforms, L = 2^8..2^16 log-uniform, 3 primes = 1 mod 2^16, "
+                   "half inverse, one persistent launch", "groups": []},
+    "c5": {"name": "polymul serving: Poisson 20k req/s, p = 998244353, degrees log-uniform 2^6..2^20",
+           "groups": []},
+    "probe": {"name": "register-only butterfly rate probe", "groups": []},
 }
 
 
@@ -131,13 +136,16 @@ def useful_bytes(groups):
 # --------------------------------------------------------------------------- ours
 
 class GPUWorkload:
-    def __init__(self, groups, torch, ntt, seed=1):
+    def __init__(self, groups, torch, ntt, seed=1, autotune=True):
         self.torch, self.ntt = torch, ntt
         self.groups = groups
         self.plans, self.bufs, self.streams, self.host = [], [], [], []
+        self.splits = []
         for gi, (p, l, b) in enumerate(groups):
             L = 1 << l
             plan = ntt.ntt_plan(p, ntt.root_of_unity(p, L), L)
+            # the library's autotuner picks the pass split for this batch size
+            self.splits.append(plan.autotune(b, use_cache=True) if autotune else list(plan.info().log_r)[:plan.info().n_passes])
             a = batch_inputs(seed + gi, b, L, p)
             view = a.view(np.int32) if a.dtype == np.uint32 else a.view(np.int64)
             t = torch.from_numpy(view.copy()).cuda()
@@ -156,11 +164,17 @@ class GPUWorkload:
         self.flush_buf.fill_(1)
 
     def step(self, events=None):
-        """Forward then inverse of every group, each pass a launch on the group's stream."""
+        """Forward then inverse of every group, each pass a launch on the group's
+        stream.  With `events`, the groups run one after another on the current
+        stream and every launch is bracketed by CUDA events (clean per-kernel
+        durations, comparable with the ncu launch list)."""
         torch, ntt = self.torch, self.ntt
         cur = torch.cuda.current_stream()
         for gi, (plan, buf, s) in enumerate(zip(self.plans, self.bufs, self.streams)):
-            s.wait_stream(cur)
+            if events is not None:
+                s = cur
+            else:
+                s.wait_stream(cur)
             b = self.groups[gi][2]
             for inv in (0, 1):
                 for k in range(self.nsteps[gi]):
@@ -171,8 +185,9 @@ class GPUWorkload:
                     if events is not None:
                         e1.record(s)
                         events.append(((gi, inv, k), e0, e1))
-        for s in self.streams:
-            cur.wait_stream(s)
+        if events is None:
+            for s in self.streams:
+                cur.wait_stream(s)
 
     def step_e2e(self):
         """Host->device copy, forward, inverse, device->host copy, per group (pinned memory)."""
@@ -305,6 +320,156 @@ def cpu_baseline_oracle(groups, budget_s=12.0):
             "sample": desc + f" of the same workload ({t:.1f} s, single thread)"}
 
 
+def run_uneven(args, dist, rank, world):
+    """Uneven batch: 4096 transforms, log2 L uniform in 8..16, three 30-bit
+    primes, half inverse, in one persistent launch (ntt_execute_uneven)
+    captured in a CUDA graph; value = butterflies/s."""
+    import torch
+    import paper_1205_2926_gb300 as ntt
+    from paper_1205_2926_gb300 import build
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    spec = uneven_batch_spec()
+    plans, descs, bfly, nbytes = {}, [], 0, 0
+    for d in spec:
+        L = 1 << d["logL"]
+        key = (d["p"], L)
+        if key not in plans:
+            plans[key] = ntt.ntt_plan(d["p"], ntt.root_of_unity(d["p"], L), L)
+        a = uniform_residues(40_000 + d["id"], L, d["p"]).astype(np.uint32)
+        t = torch.from_numpy(a.view(np.int32).copy()).cuda()
+        descs.append((plans[key], t, d["inverse"]))
+        bfly += d["logL"] * L // 2
+        nbytes += 8 * L
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ntt.ntt_execute_uneven(descs, stream=s)  # prepares the device work list
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ntt.ntt_execute_uneven(descs, stream=s)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        g.replay()
+    torch.cuda.synchronize()
+    barrier(dist)
+    peaks = load_peaks()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    ev = []
+    t0 = time.time()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    t1 = time.time()
+    clocks = sampler.stop(t0, t1)
+    assert ntt.ntt_uneven_status() == 0
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, torch)
+    K = args.steps
+    per = ms / K / 1e3
+    gbs = nbytes / per / 1e9
+    return {
+        "metric": METRIC, "value": world * bfly / per, "unit": "butterflies/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded uniform residues)",
+        "config": {"workload": WORKLOADS["c4"]["name"], "transforms": len(spec), "butterflies_per_step": bfly,
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+        "hbm_gbs_useful": gbs,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_uneven (one launch per step)"},
+        "gpu_launches": 1, "graph": "one CUDA graph replay per step", "clocks": clocks,
+    }
+
+
+def run_serving(seconds, rate, torch, ntt, seed=5, max_log=20.0):
+    """Poisson stream of polynomial products mod 998244353 (degrees
+    log-uniform in 2^6..2^max_log) through the continuous-batching server.
+    Operands are slices of one pinned pool of uniform residues; results go
+    to a pinned ring (not checked here; the tests check them).  Returns
+    latency percentiles and throughput."""
+    from paper_1205_2926_gb300.inputs import serving_trace
+    n = int(seconds * rate)
+    trace = serving_trace(seed=seed, n=n, rate_per_s=rate, dmax_log=max_log)
+    pool_words = 1 << 24
+    pool = torch.from_numpy(uniform_residues(seed, pool_words, P_NTT30).astype(np.uint32).view(np.int32)).pin_memory()
+    ring_words = 1 << 28
+    ring = torch.empty(ring_words, dtype=torch.int32).pin_memory()
+    base, rbase = pool.data_ptr(), ring.data_ptr()
+    sv = ntt.Server(P_NTT30, max_coeffs=(1 << int(max_log)) + 1, mem_budget_bytes=8 << 30, n_streams=8,
+                    max_batch=512)
+    rng = np.random.default_rng(seed)
+    offs = rng.integers(0, pool_words - (1 << 21), size=(n, 2))
+    # warm-up: one request of every length class
+    for lg in range(7, int(max_log) + 2):
+        m = (1 << (lg - 1))
+        sv.submit(base, m, base, m, rbase)
+    sv.drain(-1)
+    sv.reset_stats()
+    rpos = 0
+    t_start = time.perf_counter()
+    refused = 0
+    for i, r in enumerate(trace):
+        target = t_start + r["t_arrive_s"]
+        while time.perf_counter() < target:
+            pass
+        out_words = r["na"] + r["nb"] - 1
+        if rpos + out_words > ring_words:
+            rpos = 0
+        rc, _ = sv.submit(base + 4 * int(offs[i, 0]), r["na"], base + 4 * int(offs[i, 1]), r["nb"],
+                          rbase + 4 * rpos)
+        refused += rc != 0
+        rpos += out_words
+    t_sub = time.perf_counter() - t_start
+    sv.drain(-1)
+    st = sv.stats()
+    sv.destroy()
+    return {"requests": n, "offered_rate_per_s": rate, "submit_window_s": t_sub, "completed": int(st.completed),
+            "refused": int(st.refused) + refused * 0, "p50_ms": st.p50_us / 1e3, "p99_ms": st.p99_us / 1e3,
+            "mean_ms": st.mean_us / 1e3, "max_ms": st.max_us / 1e3,
+            "throughput_req_per_s": st.completed / st.wall_s if st.wall_s else None,
+            "butterflies_per_s": st.butterflies / st.wall_s if st.wall_s else None, "batches": int(st.batches)}
+
+
+def run_serve_workload(args, dist, rank, world):
+    import torch
+    import paper_1205_2926_gb300 as ntt
+    from paper_1205_2926_gb300 import build
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    t0 = time.time()
+    res = run_serving(args.serve_seconds, 20000.0, torch, ntt)
+    clocks = sampler.stop(t0, time.time())
+    return {
+        "metric": METRIC, "value": res["p99_ms"], "unit": "ms (p99 polymul latency)", "n_gpus": world,
+        "steps": res["requests"], "warmup": args.warmup, "ms_per_step": res["mean_ms"], "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded Poisson trace)",
+        "config": {"workload": WORKLOADS["c5"]["name"], "seconds": args.serve_seconds},
+        "serving": res, "clocks": clocks,
+    }
+
+
+def run_probe():
+    """Build and run csrc/probe/butterfly_rate.cu: register-only butterfly and
+    multiply rates of this GPU (the integer-pipe roof of the NTT kernels)."""
+    from paper_1205_2926_gb300 import build as b
+    src = os.path.join(ROOT, "paper_1205_2926_gb300", "csrc", "probe", "butterfly_rate.cu")
+    exe = os.path.join(ROOT, "paper_1205_2926_gb300", "_build", "butterfly_rate")
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run([b._nvcc(), *b.ARCH, "-O3", "-std=c++17", src, "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, check=True)
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"metric": "register-only butterflies per clock per SM", "value": res["lazy_fwd_bfly_per_clk_sm"],
+            "unit": "butterflies/clk/SM", "higher_is_better": True, "config": {"workload": "probe"}, "probe": res}
+
+
 def run_ours(args, dist, rank, world):
     import torch
     import paper_1205_2926_gb300 as ntt
@@ -386,6 +551,7 @@ def run_ours(args, dist, rank, world):
         "dtype": "u32" if groups[0][0] < (1 << 30) else "u64",
         "data": "synthetic (seeded uniform residues)",
         "config": {"workload": spec["name"], "butterflies_per_step": bfly_step,
+                   "pass_splits_log2": wl.splits,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
         "hbm_gbs_useful": world * bytes_step * K / (ms_lazy / 1e3) / 1e9,
         "ntl": {"value": ntl_value, "unit": "butterflies/s", "ms_per_step": ms_ntl / K},
@@ -398,6 +564,8 @@ def run_ours(args, dist, rank, world):
         "graph": "timed steps are CUDA graph replays; kernel times from an eager pass with events",
         "clocks": clocks,
     }
+    if not args.no_serving and args.workload == "c2":
+        line["polymul_serving"] = run_serving(args.serve_seconds, 20000.0, torch, ntt)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(groups)
     return line
@@ -409,6 +577,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     spec = WORKLOADS[args.workload]
+    if args.workload in ("c4", "c5"):
+        return run_reference_sampled(args, world)
     groups = spec["groups"]
     budget = max(0.5, min(6.0, 60.0 / max(args.steps + args.warmup, 1)))
     for _ in range(args.warmup):
@@ -433,6 +603,60 @@ def run_reference(args, rank, world):
     }
 
 
+def run_reference_sampled(args, world):
+    """Oracle on a bounded sample of the uneven batch (c4: transforms of the
+    spec in order, forward or inverse as specified) or of the serving trace
+    (c5: products through the oracle's convolution, one after another)."""
+    import oracle
+    o = oracle.get()
+    budget = max(1.0, min(20.0, 60.0 / max(args.steps + args.warmup, 1) * args.steps))
+    if args.workload == "c4":
+        spec = uneven_batch_spec()
+        bf, t, n = 0, 0.0, 0
+        for d in spec:
+            if t > budget:
+                break
+            L = 1 << d["logL"]
+            a = uniform_residues(40_000 + d["id"], L, d["p"])
+            w = o.root_of_unity(d["p"], L)
+            t0 = time.perf_counter()
+            (o.intt_ref if d["inverse"] else o.ntt_ref)(d["p"], w, a)
+            t += time.perf_counter() - t0
+            bf += d["logL"] * L // 2
+            n += 1
+        value, unit, hib = bf / t, "butterflies/s", True
+        sample = f"first {n} of 4096 transforms of the uneven batch ({t:.1f} s, single thread)"
+        extra = {}
+    else:
+        from paper_1205_2926_gb300.inputs import serving_trace
+        trace = serving_trace(n=100000, rate_per_s=20000.0)
+        lat, t = [], 0.0
+        for r in trace:
+            if t > budget:
+                break
+            a = uniform_residues(r["id"], r["na"], P_NTT30)
+            b = uniform_residues(r["id"] + 1, r["nb"], P_NTT30)
+            t0 = time.perf_counter()
+            o.polymul_ntt(P_NTT30, a, b)
+            dt = time.perf_counter() - t0
+            t += dt
+            lat.append(dt * 1e3)
+        lat = np.array(lat)
+        value, unit, hib = float(np.percentile(lat, 99)), "ms (p99 polymul latency)", False
+        sample = f"{len(lat)} products of the serving trace, one at a time, no queueing ({t:.1f} s, single thread)"
+        extra = {"serving": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": value, "requests": len(lat)}}
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": hib, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+        "config": {"workload": WORKLOADS[args.workload]["name"]},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    line.update(extra)
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -441,12 +665,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
+    if args.impl == "reference" and args.workload == "probe":
+        print(json.dumps({"impl": "reference", "unavailable": "the probe measures GPU pipes only"}))
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
         if line is not None:
@@ -457,7 +686,14 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    line = run_ours(args, dist, rank, world)
+    if args.workload == "probe":
+        line = run_probe()
+    elif args.workload == "c4":
+        line = run_uneven(args, dist, rank, world)
+    elif args.workload == "c5":
+        line = run_serve_workload(args, dist, rank, world)
+    else:
+        line = run_ours(args, dist, rank, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

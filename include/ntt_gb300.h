@@ -109,11 +109,22 @@ typedef struct {
 int ntt_plan_get_info(ntt_plan_t plan, ntt_plan_info_t *info);
 
 /* Override the pass split (autotuning; n_passes 1..4, sum of log_r = log L,
- * every log_r[i] in [3, 12], column passes (all but the last) at most 10 and
+ * every log_r[i] in [3, 11], and every column pass (all but the last)
  * followed by at least 2^5 (32-bit words) or 2^4 (64-bit words) elements).
  * Rebuilds the plan's middle-twiddle tables.  NTT_ERR_ARG if the split is not
  * allowed. */
 int ntt_plan_set_split(ntt_plan_t plan, int n_passes, const int *log_r);
+
+/* Autotuner: time every allowed pass split of this plan (forward + inverse
+ * on a scratch batch of `batch` vectors, CUDA events, after warm-up), keep
+ * the fastest, and store it in a JSON cache keyed by GPU name, word size,
+ * log L and log2(batch) ($NTT_AUTOTUNE_CACHE, default
+ * ~/.cache/ntt_gb300_autotune.json).  With use_cache != 0 a cached choice
+ * for the same key is applied without timing.  log_r_out (may be NULL, else
+ * room for 4 ints) receives the chosen split.  Allocates a scratch batch
+ * and synchronises; call at set-up time.  Errors: NTT_ERR_ARG, NTT_ERR_NOMEM,
+ * NTT_ERR_CUDA. */
+int ntt_plan_autotune(ntt_plan_t plan, size_t batch, int use_cache, int *log_r_out);
 
 /* ------------------------------------------------------------- transforms */
 

@@ -87,6 +87,13 @@ class Plan:
         arr = (ctypes.c_int * len(log_r))(*log_r)
         check(_lib.load().ntt_plan_set_split(self.handle, len(log_r), arr), "ntt_plan_set_split")
 
+    def autotune(self, batch: int, use_cache: bool = True) -> list:
+        """Time every allowed pass split for this batch size, keep the fastest
+        (cached per GPU model and shape); returns the chosen split."""
+        out = (ctypes.c_int * 4)()
+        check(_lib.load().ntt_plan_autotune(self.handle, batch, int(use_cache), out), "ntt_plan_autotune")
+        return [v for v in out if v][: self.info().n_passes]
+
     def destroy(self) -> None:
         if getattr(self, "handle", None):
             check(_lib.load().ntt_plan_destroy(self.handle), "ntt_plan_destroy")

@@ -94,14 +94,59 @@ NTT_HD void bfly_fwd_ntl(W &x, W &y, W w, W wq, W p) {
     y = r;
 }
 
+// x - c if x >= c else x, written as a compare and select (same result as
+// csub for 0 <= x < 2c); on sm_103a this form schedules better in the
+// butterfly than the unsigned minimum.
+template <typename W>
+NTT_HD W csub_sel(W x, W c) {
+    return x >= c ? (W)(x - c) : x;
+}
+
 // Algorithm 3 (modified Shoup butterfly): X, Y in [0, 2p), p < beta/4;
 // X' = X + Y reduced once by 2p, T = X - Y + 2p in [0, 4p) without any test,
 // Y' = W T - Q p in [0, 2p) without the final correction.
 template <typename W>
 NTT_HD void bfly_fwd_lazy(W &x, W &y, W w, W wq, W p, W p2) {
-    W s = csub((W)(x + y), p2);
+    W s = csub_sel((W)(x + y), p2);
     W t = (W)(x - y + p2);
     y = shoup_mul(t, w, wq, p);
+    x = s;
+}
+
+// Butterflies with W = 1 (the stage of distance 1, and the k = 0 pairs of
+// other stages; Section 5 notes L - 1 of them per transform).  Same outputs
+// and ranges as the general butterflies with W = 1, without the product:
+// forward lazy: Y' = T reduced once from [0, 4p) to [0, 2p);
+// inverse lazy: T = Y reduced once from [0, 4p) to [0, 2p).
+template <typename W>
+NTT_HD void bfly_fwd_lazy_w1(W &x, W &y, W p2) {
+    W s = csub_sel((W)(x + y), p2);
+    W t = (W)(x - y + p2);
+    y = csub_sel(t, p2);
+    x = s;
+}
+
+template <typename W>
+NTT_HD void bfly_fwd_ntl_w1(W &x, W &y, W p) {
+    W s = csub((W)(x + y), p);
+    W t = (W)(x - y);
+    y = umin(t, (W)(t + p));
+    x = s;
+}
+
+template <typename W>
+NTT_HD void bfly_inv_lazy_w1(W &x, W &y, W p2) {
+    W a = csub(x, p2);
+    W t = csub(y, p2);
+    x = (W)(a + t);
+    y = (W)(a - t + p2);
+}
+
+template <typename W>
+NTT_HD void bfly_inv_ntl_w1(W &x, W &y, W p) {
+    W s = csub((W)(x + y), p);
+    W d = (W)(x - y);
+    y = umin(d, (W)(d + p));
     x = s;
 }
 

@@ -1,0 +1,188 @@
+// ntt_autotune.cu -- picks the pass split of a plan by timing candidates on
+// the device, and remembers the choice in a small JSON cache file.
+//
+// A candidate is a split of log L into passes (the radix of each on-chip
+// sub-transform); the kernel geometry of each pass (tile width, rows per
+// CTA) follows from it.  Every candidate runs forward + inverse on a scratch
+// batch, timed with CUDA events after warm-up; the fastest is kept.  The
+// cache key is (GPU name, word size, log L, log2 of the batch rounded down),
+// so one tuning serves every plan of that shape on that GPU model.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "ntt_internal.hpp"
+
+namespace ntt {
+
+static std::mutex g_tune_mu;
+
+static std::string cache_path() {
+    const char *p = getenv("NTT_AUTOTUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/ntt_gb300_autotune.json";
+}
+
+// The cache is a flat JSON object {"key": [l0, l1, ...], ...}.
+static std::map<std::string, std::vector<int>> load_cache() {
+    std::map<std::string, std::vector<int>> m;
+    std::ifstream f(cache_path());
+    if (!f) return m;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    size_t i = 0;
+    while (true) {
+        size_t k0 = s.find('"', i);
+        if (k0 == std::string::npos) break;
+        size_t k1 = s.find('"', k0 + 1);
+        size_t a0 = s.find('[', k1), a1 = s.find(']', a0);
+        if (k1 == std::string::npos || a0 == std::string::npos || a1 == std::string::npos) break;
+        std::vector<int> v;
+        std::stringstream vs(s.substr(a0 + 1, a1 - a0 - 1));
+        std::string tok;
+        while (std::getline(vs, tok, ',')) v.push_back(atoi(tok.c_str()));
+        m[s.substr(k0 + 1, k1 - k0 - 1)] = v;
+        i = a1 + 1;
+    }
+    return m;
+}
+
+static void save_cache(const std::map<std::string, std::vector<int>> &m) {
+    const std::string path = cache_path();
+    // create the parent directories (mkdir -p)
+    for (size_t pos = path.find('/', 1); pos != std::string::npos; pos = path.find('/', pos + 1))
+        mkdir(path.substr(0, pos).c_str(), 0755);
+    const std::string tmp = path + ".tmp";
+    std::ofstream f(tmp);
+    if (!f) return;
+    f << "{\n";
+    size_t n = 0;
+    for (auto &kv : m) {
+        f << "  \"" << kv.first << "\": [";
+        for (size_t i = 0; i < kv.second.size(); ++i) f << (i ? ", " : "") << kv.second[i];
+        f << "]" << (++n < m.size() ? "," : "") << "\n";
+    }
+    f << "}\n";
+    f.close();
+    rename(tmp.c_str(), path.c_str());
+}
+
+static std::string tune_key(const ntt_plan_s *pl, size_t batch) {
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, pl->device);
+    int lb = 0;
+    while ((2ull << lb) <= batch) ++lb;
+    std::string name = prop.name;
+    for (char &c : name)
+        if (c == '"' || c == ' ') c = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s/w%d/l%d/b%d", name.c_str(), pl->wbytes * 8, pl->logL, lb);
+    return buf;
+}
+
+// Candidate splits: one pass when it fits, every two-pass split, and a few
+// balanced three-pass splits for long transforms.
+static std::vector<std::vector<int>> candidates(const ntt_plan_s *pl) {
+    std::vector<std::vector<int>> c;
+    const int l = pl->logL;
+    auto push = [&](std::vector<int> v) {
+        int n = (int)v.size();
+        if (split_allowed(l, pl->wbytes, n, v.data())) c.push_back(v);
+    };
+    if (l <= kMaxRowLog) push({l});
+    for (int a = 3; a <= kMaxColLog; ++a) push({a, l - a});
+    for (int a = 3; a <= kMaxColLog; ++a)
+        for (int b = 3; b <= kMaxColLog; ++b)
+            if (l - a - b >= 6 && l - a - b <= kMaxRowLog && std::abs(a - b) <= 1) push({a, b, l - a - b});
+    return c;
+}
+
+}  // namespace ntt
+
+using namespace ntt;
+
+extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int *log_r_out) {
+    if (!pl || batch == 0) return NTT_ERR_ARG;
+    if (pl->logL <= 2) return NTT_OK;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const std::string key = tune_key(pl, batch);
+    if (use_cache) {
+        auto m = load_cache();
+        auto it = m.find(key);
+        if (it != m.end() && split_allowed(pl->logL, pl->wbytes, (int)it->second.size(), it->second.data())) {
+            int rc = ntt_plan_set_split(pl, (int)it->second.size(), it->second.data());
+            if (rc == NTT_OK && log_r_out)
+                for (size_t i = 0; i < it->second.size(); ++i) log_r_out[i] = it->second[i];
+            return rc;
+        }
+    }
+    const size_t words = batch * pl->L;
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, words * pl->wbytes);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "autotune buffer");
+    cudaMemset(buf, 0, words * pl->wbytes);
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int saved_variant = pl->variant;
+    pl->variant = NTT_VARIANT_LAZY;
+    std::vector<int> best;
+    float best_ms = 1e30f;
+    int rc = NTT_OK;
+    for (const auto &cand : candidates(pl)) {
+        rc = ntt_plan_set_split(pl, (int)cand.size(), cand.data());
+        if (rc) break;
+        for (int w = 0; w < 2; ++w) {
+            enqueue_transform(pl, 0, buf, batch, pl->L, st);
+            enqueue_transform(pl, 1, buf, batch, pl->L, st);
+        }
+        cudaEventRecord(e0, st);
+        const int reps = 5;
+        for (int r = 0; r < reps; ++r) {
+            enqueue_transform(pl, 0, buf, batch, pl->L, st);
+            enqueue_transform(pl, 1, buf, batch, pl->L, st);
+        }
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "autotune timing");
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand;
+        }
+    }
+    pl->variant = saved_variant;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(buf);
+    if (rc) return rc;
+    if (best.empty()) return NTT_ERR_ARG;
+    rc = ntt_plan_set_split(pl, (int)best.size(), best.data());
+    if (rc) return rc;
+    if (log_r_out)
+        for (size_t i = 0; i < best.size(); ++i) log_r_out[i] = best[i];
+    auto m = load_cache();
+    m[key] = best;
+    save_cache(m);
+    return NTT_OK;
+}

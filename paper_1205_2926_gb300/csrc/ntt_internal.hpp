@@ -13,8 +13,8 @@
 namespace ntt {
 
 constexpr int kMaxPasses = 4;
-constexpr int kMaxRowLog = 12;  // longest on-chip sub-transform of a row pass
-constexpr int kMaxColLog = 10;  // longest column-pass sub-transform
+constexpr int kMaxRowLog = 11;  // longest on-chip sub-transform of a row pass
+constexpr int kMaxColLog = 11;  // longest column-pass sub-transform
 
 // Host number theory (the library's own; independent of any test code).
 namespace nt {
@@ -89,6 +89,9 @@ int enqueue_transform(ntt_plan_s *plan, int dir, void *data, size_t batch, size_
 // one pass; the inverse executes the passes in reverse order).
 int enqueue_steps(ntt_plan_s *plan, int dir, void *data, size_t batch, size_t stride, cudaStream_t st, int first,
                   int count);
+
+// Whether a pass split is allowed for a transform of 2^logL words of wbytes.
+bool split_allowed(int logL, int wbytes, int n, const int *logr);
 
 // Record a CUDA failure for ntt_last_cuda_error(); returns NTT_ERR_CUDA.
 int cuda_fail(cudaError_t e, const char *where);

@@ -22,12 +22,13 @@
 // than m - 1) keeps runs of consecutive k 16-byte aligned for vector loads.
 //
 // On-chip work.  A CTA stages a tile in shared memory as 16-byte vectors of
-// V words (V = 4 for 32-bit, 2 for 64-bit words):
-//   column pass: a vector holds V adjacent columns, i.e. the same element of
-//     V independent sub-transforms, which share every twiddle;
-//   row pass: a vector holds V consecutive elements of one row; the stages
-//     on the low log2(V) index bits run inside the vector ("lane stages"),
-//     the others on whole vectors with one twiddle per lane.
+// V words (V = 4 for 32-bit, 2 for 64-bit words); the V lanes of a vector
+// are the same element of V independent sub-transforms, so they share every
+// twiddle:
+//   column pass: lanes are V adjacent columns (one 16-byte global chunk);
+//   row pass: lanes are V consecutive rows; the copy into shared memory
+//     transposes (one word per cp.async), and the forward pass's last round
+//     writes eight consecutive words of each row straight to HBM.
 // Each thread holds E = 8 vectors in registers and runs up to three
 // butterfly stages per round (radix-8 blocks); rounds exchange vectors
 // through shared memory.  The vector of row s sits at chunk
@@ -93,6 +94,14 @@ __device__ __forceinline__ void cp_async16(uint4 *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Copy of one 4- or 8-byte word (the transposing row copies).
+template <typename W>
+__device__ __forceinline__ void cp_async_word(W *dst, const W *src) {
+    if (sizeof(W) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
@@ -171,6 +180,22 @@ __device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2) {
     }
 }
 
+// Butterfly with W = 1 (no product; see modarith.cuh).
+template <typename W, int DIR, int VAR>
+__device__ __forceinline__ void bfly_w1(W &x, W &y, W p, W p2) {
+    if (DIR == DIR_FWD) {
+        if (VAR == VAR_LAZY)
+            bfly_fwd_lazy_w1(x, y, p2);
+        else
+            bfly_fwd_ntl_w1(x, y, p);
+    } else {
+        if (VAR == VAR_LAZY)
+            bfly_inv_lazy_w1(x, y, p2);
+        else
+            bfly_inv_ntl_w1(x, y, p);
+    }
+}
+
 template <typename W, int VAR>
 __device__ __forceinline__ W mul_twiddle(W x, W w, W wq, W p) {
     W y = shoup_mul(x, w, wq, p);  // any x < beta -> [0, 2p)
@@ -197,20 +222,30 @@ struct Sched {
     }
 };
 
-// Butterfly stages of one round on E vectors held in registers.  twp points
-// at tw + (low index bits of the unit); QUAD takes one twiddle per lane.
-template <typename W, int DIR, int VAR, int LE, int B0, int NST, bool QUAD>
+// Butterfly stages of one round on E vectors held in registers; the V lanes
+// of a vector share every twiddle.  twp points at tw + (low index bits of
+// the unit).  In the round with b0 = 0 the pairs with jl = 0 have k = 0 for
+// every unit, hence W = 1: they skip the product.
+// SKIP1 leaves out the stage of distance 1 (lb = 0 in the round with
+// b0 = 0), which the caller fuses with the middle twiddle.
+template <typename W, int DIR, int VAR, int LE, int B0, int NST, bool SKIP1 = false>
 __device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W *__restrict__ twp, W p, W p2) {
     constexpr int V = Lanes<W>::V;
     constexpr int E = 1 << LE;
-    constexpr int B0S = QUAD ? B0 + Lanes<W>::LOGV : B0;  // bit position in element-index space
 #pragma unroll
     for (int step = 0; step < NST; ++step) {
         const int lb = DIR == DIR_FWD ? LE - 1 - step : LE - NST + step;
+        if (SKIP1 && B0 == 0 && lb == 0) continue;
 #pragma unroll
         for (int jl = 0; jl < (1 << lb); ++jl) {
-            const int off = (1 << (B0S + lb)) + (jl << B0S);
-            if (!QUAD) {
+            const int off = (1 << (B0 + lb)) + (jl << B0);
+            if (B0 == 0 && jl == 0) {
+#pragma unroll
+                for (int jh = 0; jh < E; jh += (2 << lb)) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) bfly_w1<W, DIR, VAR>(x[jh][v], x[jh + (1 << lb)][v], p, p2);
+                }
+            } else {
                 W w, wq;
                 ld_pair(twp, off, w, wq);
 #pragma unroll
@@ -219,57 +254,20 @@ __device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W
                     for (int v = 0; v < V; ++v)
                         bfly<W, DIR, VAR>(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w, wq, p, p2);
                 }
-            } else {
-                W w[V], wq[V];
-                ld_pairs<W>(twp, off, w, wq);
-#pragma unroll
-                for (int jh = 0; jh < E; jh += (2 << lb)) {
-#pragma unroll
-                    for (int v = 0; v < V; ++v)
-                        bfly<W, DIR, VAR>(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w[v], wq[v], p, p2);
-                }
             }
-        }
-    }
-}
-
-// Twiddles of the lane stages (element-index bits below log2 V): tw[1]
-// (distance 1) and tw[2], tw[3] (distance 2, 32-bit words only).
-template <typename W>
-struct LaneTw {
-    W w[3], wq[3];
-};
-
-template <typename W, int DIR, int VAR, int E>
-__device__ __forceinline__ void lane_stages(W (&x)[E][Lanes<W>::V], const LaneTw<W> &lt, W p, W p2) {
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-        if (Lanes<W>::V == 4) {
-            if (DIR == DIR_FWD) {
-                bfly<W, DIR, VAR>(x[j][0], x[j][2], lt.w[1], lt.wq[1], p, p2);
-                bfly<W, DIR, VAR>(x[j][1], x[j][3], lt.w[2], lt.wq[2], p, p2);
-                bfly<W, DIR, VAR>(x[j][0], x[j][1], lt.w[0], lt.wq[0], p, p2);
-                bfly<W, DIR, VAR>(x[j][2], x[j][3], lt.w[0], lt.wq[0], p, p2);
-            } else {
-                bfly<W, DIR, VAR>(x[j][0], x[j][1], lt.w[0], lt.wq[0], p, p2);
-                bfly<W, DIR, VAR>(x[j][2], x[j][3], lt.w[0], lt.wq[0], p, p2);
-                bfly<W, DIR, VAR>(x[j][0], x[j][2], lt.w[1], lt.wq[1], p, p2);
-                bfly<W, DIR, VAR>(x[j][1], x[j][3], lt.w[2], lt.wq[2], p, p2);
-            }
-        } else {
-            bfly<W, DIR, VAR>(x[j][0], x[j][1], lt.w[0], lt.wq[0], p, p2);
         }
     }
 }
 
 template <typename W, int DIR, int VAR, int E>
 __device__ __forceinline__ void normalize(W (&x)[E][Lanes<W>::V], W p, W p2) {
-    if (VAR != VAR_LAZY) return;
+    if constexpr (VAR == VAR_LAZY) {
 #pragma unroll
-    for (int j = 0; j < E; ++j)
+        for (int j = 0; j < E; ++j)
 #pragma unroll
-        for (int v = 0; v < Lanes<W>::V; ++v)
-            x[j][v] = DIR == DIR_FWD ? reduce2(x[j][v], p) : reduce4(x[j][v], p, p2);
+            for (int v = 0; v < Lanes<W>::V; ++v)
+                x[j][v] = DIR == DIR_FWD ? reduce2(x[j][v], p) : reduce4(x[j][v], p, p2);
+    }
 }
 
 // Middle twiddle of a column pass, omega^((L/B) c rev(s)), on the E vectors
@@ -298,30 +296,84 @@ __device__ __forceinline__ void middle_twiddle(W (&x)[E][Lanes<W>::V], uint32_t 
     }
 }
 
+// Distance-1 stage (W = 1) fused with the middle twiddle of a forward column
+// pass: X' = M_s (X + Y), Y' = M_{s+1} (X - Y + 2p).  Shoup's product accepts
+// any input below beta, so the two reductions of the W = 1 butterfly go away
+// (lazy variant; the NTL variant keeps its reductions).
+template <typename W, int VAR, int E>
+__device__ __forceinline__ void last_stage_and_twiddle(W (&x)[E][Lanes<W>::V], uint32_t s0, uint32_t c0, uint32_t R,
+                                                       const PassArgs<W> &a) {
+    constexpr int V = Lanes<W>::V;
+    const W p2 = (W)(2 * a.p);
+#pragma unroll
+    for (int j = 0; j < E; j += 2) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (VAR == VAR_LAZY) {
+                const W s = (W)(x[j][v] + x[j + 1][v]);
+                const W t = (W)(x[j][v] - x[j + 1][v] + p2);
+                x[j][v] = s;
+                x[j + 1][v] = t;
+            } else {
+                bfly_w1<W, DIR_FWD, VAR>(x[j][v], x[j + 1][v], a.p, p2);
+            }
+        }
+    }
+    middle_twiddle<W, VAR, E>(x, s0, c0, R, a);
+}
+
+// Inverse counterpart: the middle twiddle leaves every value in [0, 2p)
+// (lazy), so the following W = 1 butterfly needs no reduction:
+// X' = X + Y, Y' = X - Y + 2p.
+template <typename W, int VAR, int E>
+__device__ __forceinline__ void twiddle_and_first_stage(W (&x)[E][Lanes<W>::V], uint32_t s0, uint32_t c0, uint32_t R,
+                                                        const PassArgs<W> &a) {
+    constexpr int V = Lanes<W>::V;
+    const W p2 = (W)(2 * a.p);
+    middle_twiddle<W, VAR, E>(x, s0, c0, R, a);
+#pragma unroll
+    for (int j = 0; j < E; j += 2) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (VAR == VAR_LAZY) {
+                const W s = (W)(x[j][v] + x[j + 1][v]);
+                const W t = (W)(x[j][v] - x[j + 1][v] + p2);
+                x[j][v] = s;
+                x[j + 1][v] = t;
+            } else {
+                bfly_w1<W, DIR_INV, VAR>(x[j][v], x[j + 1][v], a.p, p2);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ tile geometry
 
 // Column pass: CTA iteration `tile` covers sub-tiles tile*per_cta + ti, each
 // R rows x TV vectors of one block; 2^ltb sub-tiles per block, 2^lbt blocks
-// per transform.  Row pass: iteration `tile` covers rows tile*per_cta + r.
-template <typename W, int LOGR, bool ROW>
+// per transform.  Row pass: iteration `tile` covers vector groups
+// tile*per_cta + ti; group ti holds V consecutive rows, one per lane.
+template <typename W, int LOGR, bool ROW, int TVC = -1>
 struct Geo {
-    static constexpr int LOGS = ROW ? LOGR - Lanes<W>::LOGV : LOGR;  // vector-index bits
+    static constexpr int LOGS = LOGR;                                // element-index bits
     static constexpr uint32_t NS = 1u << LOGS;                       // vectors per sub-transform
     static constexpr uint32_t NSP = NS + (NS >> 3);                  // with padding
     using S = Sched<LOGS>;
-    // The last round stores straight from registers when its vectors are
-    // contiguous across neighbouring threads: always for a column pass, and
-    // for the inverse row pass once eight neighbouring threads hold
-    // neighbouring vectors (b0 >= 3).
-    __host__ __device__ static constexpr bool DIRECT_STORE(int dir) {
-        return !ROW || (dir == DIR_INV && S::b0(DIR_INV, S::NR - 1) >= 3);
-    }
+    // The last round stores straight from registers where that is
+    // coalesced: always in a column pass (neighbouring threads hold
+    // neighbouring column vectors), and in the forward row pass (each thread
+    // holds eight consecutive elements of each of its rows).
+    __host__ __device__ static constexpr bool DIRECT_STORE(int dir) { return !ROW || dir == DIR_FWD; }
 
-    int logTV, ltb, lbt;
+    int logTV_, ltb, lbt;
     uint32_t sub_total;  // column pass: sub-tiles in the pass
 
+    // log2 of the tile width in vectors: a compile-time constant for row
+    // passes and for the common column-pass width, else the runtime value
+    __device__ __forceinline__ int logTV() const { return ROW ? 0 : (TVC >= 0 ? TVC : logTV_); }
+
     __device__ __forceinline__ explicit Geo(const PassArgs<W> &a) {
-        logTV = ROW ? 0 : a.logTV;
+        logTV_ = ROW ? 0 : a.logTV;
         ltb = ROW ? 0 : a.logS - a.logTV - Lanes<W>::LOGV;
         lbt = ROW ? 0 : a.logL - LOGR - a.logS;
         sub_total = ROW ? 0 : (a.batch << (ltb + lbt));
@@ -331,7 +383,7 @@ struct Geo {
         ct = t & ((1u << ltb) - 1u);
         const uint32_t blk = (t >> ltb) & ((1u << lbt) - 1u), b = t >> (ltb + lbt);
         return a.data + (uint64_t)b * a.stride + ((uint64_t)blk << (LOGR + a.logS)) +
-               ((uint64_t)ct << (logTV + Lanes<W>::LOGV));
+               ((uint64_t)ct << (logTV() + Lanes<W>::LOGV));
     }
     __device__ __forceinline__ W *row_ptr(const PassArgs<W> &a, uint64_t row) const {
         if (a.rowptrs) return a.rowptrs[row];
@@ -346,47 +398,44 @@ struct Geo {
 // and writes 16-byte vectors.  Consecutive threads take consecutive 16-byte
 // chunks of a row, so both directions are coalesced; addresses advance by
 // constant strides from a per-thread base.
-template <typename W, int LOGR, bool ROW, bool STORE>
-__device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOGR, ROW> &geo, uint32_t tile,
+template <typename W, int LOGR, bool ROW, bool STORE, int TVC>
+__device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
                                           uint4 *buf) {
-    using G = Geo<W, LOGR, ROW>;
+    using G = Geo<W, LOGR, ROW, TVC>;
     constexpr int V = Lanes<W>::V;
     if (ROW) {
-        const uint64_t row0 = (uint64_t)tile * a.per_cta;
-        if (G::NS >= (uint32_t)kThreads) {
-            // whole rows, kThreads chunks per step
-            for (int r = 0; r < a.per_cta; ++r) {
-                if (row0 + r >= a.nrows) break;
-                W *g = geo.row_ptr(a, row0 + r) + threadIdx.x * V;
-                uint4 *sp = buf + r * G::NSP + threadIdx.x + (threadIdx.x >> 3);
-#pragma unroll 4
-                for (uint32_t q = threadIdx.x; q < G::NS; q += kThreads) {
-                    if (STORE)
-                        *reinterpret_cast<uint4 *>(g) = *sp;
-                    else
-                        cp_async16(sp, g);
-                    g += kThreads * V;
-                    sp += kThreads + kThreads / 8;
+        // element s of row v of group gi <-> word v of chunk s + s/8 of the
+        // group's region; each 16-byte global chunk moves as V copies of one
+        // word (the transposition into lanes happens in the copy)
+        constexpr int LOGV = Lanes<W>::LOGV;
+        constexpr uint32_t NCH = (1u << LOGR) >> LOGV;  // 16-byte chunks per row
+        const uint64_t row0 = (uint64_t)tile * a.per_cta * V;
+        const uint32_t total = ((uint32_t)a.per_cta << LOGV) * NCH;
+        for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
+            const uint32_t c = i & (NCH - 1), rv = i / NCH;
+            const uint64_t row = row0 + rv;
+            if (row >= a.nrows) continue;
+            W *g = geo.row_ptr(a, row) + c * V;
+            W *base = reinterpret_cast<W *>(buf + (rv >> LOGV) * G::NSP) + (rv & (V - 1));
+            if (STORE) {
+                uint4 q;
+                W *pq = reinterpret_cast<W *>(&q);
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const uint32_t e = c * V + k;
+                    pq[k] = base[(e + (e >> 3)) * V];
                 }
-            }
-        } else {
-            // several rows per step: chunk q of row r
-            constexpr uint32_t rows_step = kThreads >> G::LOGS;
-            const uint32_t q = threadIdx.x & (G::NS - 1);
-            uint4 *sp = buf + (threadIdx.x >> G::LOGS) * G::NSP + q + (q >> 3);
-            for (uint32_t r = threadIdx.x >> G::LOGS; r < (uint32_t)a.per_cta; r += rows_step) {
-                if (row0 + r < a.nrows) {
-                    W *g = geo.row_ptr(a, row0 + r) + q * V;
-                    if (STORE)
-                        *reinterpret_cast<uint4 *>(g) = *sp;
-                    else
-                        cp_async16(sp, g);
+                *reinterpret_cast<uint4 *>(g) = q;
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const uint32_t e = c * V + k;
+                    cp_async_word<W>(base + (e + (e >> 3)) * V, g + k);
                 }
-                sp += rows_step * G::NSP;
             }
         }
     } else {
-        const int logTV = geo.logTV;
+        const int logTV = geo.logTV();
         const uint32_t cc = threadIdx.x & ((1u << logTV) - 1u);
         const uint32_t rows_step = (uint32_t)kThreads >> logTV;  // >= 32, a multiple of 8
         const uint64_t S = 1ull << a.logS;
@@ -413,17 +462,17 @@ __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOG
 }
 
 // One round over the tile in shared memory (compile-time round index RI).
-template <typename W, int DIR, int VAR, int LOGR, bool ROW, int RI>
-__device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LOGR, ROW> &geo, uint32_t tile,
-                                           uint4 *buf, const LaneTw<W> &lt) {
-    using G = Geo<W, LOGR, ROW>;
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC, int RI>
+__device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
+                                           uint4 *buf) {
+    using G = Geo<W, LOGR, ROW, TVC>;
     using S = typename G::S;
     constexpr int V = Lanes<W>::V;
     constexpr int LE = S::LE, E = S::E;
     constexpr int B0 = S::b0(DIR, RI), NST = S::nst(DIR, RI);
     constexpr bool FIRST = RI == 0, LAST = RI == S::NR - 1;
     const W p = a.p, p2 = (W)(2 * a.p);
-    const int logTV = geo.logTV;
+    const int logTV = geo.logTV();
     const uint32_t units = (uint32_t)a.per_cta << (G::LOGS - LE + logTV);
     for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
         const uint32_t tv = u & ((1u << logTV) - 1u);
@@ -445,25 +494,38 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
             geo.col_origin(a, tile * a.per_cta + ti, ct);
             c0 = ((ct << logTV) + tv) * V;
         }
-        if (DIR == DIR_INV && FIRST) {
-            if (mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
-            if (ROW) lane_stages<W, DIR, VAR, E>(x, lt, p, p2);
-        }
-        const W *twp = a.tw + 2 * (ROW ? (lo << Lanes<W>::LOGV) : lo);
-        round_regs<W, DIR, VAR, LE, B0, NST, ROW>(x, twp, p, p2);
-        if (DIR == DIR_FWD && LAST) {
-            if (ROW) lane_stages<W, DIR, VAR, E>(x, lt, p, p2);
-            if (mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+        // rounds holding the distance-1 stage (b0 = 0) of a column pass fuse
+        // it with the middle twiddle; every other round runs as is
+        constexpr bool FUSE = !ROW && B0 == 0 && LE == 3 &&
+                              ((DIR == DIR_INV && FIRST) || (DIR == DIR_FWD && LAST));
+        if (FUSE && mid) {
+            if (DIR == DIR_INV) twiddle_and_first_stage<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+            round_regs<W, DIR, VAR, LE, B0, NST, true>(x, a.tw + 2 * lo, p, p2);
+            if (DIR == DIR_FWD) last_stage_and_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+        } else {
+            if (DIR == DIR_INV && FIRST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+            round_regs<W, DIR, VAR, LE, B0, NST>(x, a.tw + 2 * lo, p, p2);
+            if (DIR == DIR_FWD && LAST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
         }
         if (LAST && (a.flags & F_NORMALIZE)) normalize<W, DIR, VAR, E>(x, p, p2);
         if (LAST && G::DIRECT_STORE(DIR)) {
             // last round writes straight to HBM (coalesced for this layout)
             if (ROW) {
-                const uint64_t row = (uint64_t)tile * a.per_cta + ti;
-                if (row < a.nrows) {
-                    W *gp = geo.row_ptr(a, row) + s0 * V;
+                // b0 = 0: elements s0 .. s0+7 of each lane's row, 8 consecutive words
+                const uint64_t row0 = ((uint64_t)tile * a.per_cta + ti) * V;
 #pragma unroll
-                    for (int j = 0; j < E; ++j) *reinterpret_cast<uint4 *>(gp + ((j << B0) * V)) = pack<W>(x[j]);
+                for (int v = 0; v < V; ++v) {
+                    if (row0 + v < a.nrows) {
+                        W *gp = geo.row_ptr(a, row0 + v) + s0;
+#pragma unroll
+                        for (int q = 0; q < E; q += V) {
+                            uint4 c;
+                            W *pc = reinterpret_cast<W *>(&c);
+#pragma unroll
+                            for (int k = 0; k < V; ++k) pc[k] = x[q + k][v];
+                            *reinterpret_cast<uint4 *>(gp + q) = c;
+                        }
+                    }
                 }
             } else {
                 const uint32_t t = tile * a.per_cta + ti;
@@ -486,48 +548,51 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
     }
 }
 
-template <typename W, int DIR, int VAR, int LOGR, bool ROW, int RI = 0>
-__device__ __forceinline__ void tile_rounds(const PassArgs<W> &a, const Geo<W, LOGR, ROW> &geo, uint32_t tile,
-                                            uint4 *buf, const LaneTw<W> &lt) {
-    tile_round<W, DIR, VAR, LOGR, ROW, RI>(a, geo, tile, buf, lt);
-    if constexpr (RI + 1 < Geo<W, LOGR, ROW>::S::NR) {
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC, int RI = 0>
+__device__ __forceinline__ void tile_rounds(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
+                                            uint4 *buf) {
+    tile_round<W, DIR, VAR, LOGR, ROW, TVC, RI>(a, geo, tile, buf);
+    if constexpr (RI + 1 < Geo<W, LOGR, ROW, TVC>::S::NR) {
         __syncthreads();
-        tile_rounds<W, DIR, VAR, LOGR, ROW, RI + 1>(a, geo, tile, buf, lt);
+        tile_rounds<W, DIR, VAR, LOGR, ROW, TVC, RI + 1>(a, geo, tile, buf);
     }
 }
 
-template <typename W>
-__device__ __forceinline__ LaneTw<W> load_lane_tw(const W *tw) {
-    LaneTw<W> lt;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) ld_pair(tw, 1 + i, lt.w[i], lt.wq[i]);
-    return lt;
-}
+// Widest column tile for a sub-transform length: R * TV <= 2048 vectors per
+// shared buffer, at most 8 vectors (128 bytes) per row.
+template <int LOGR>
+struct ColWidth {
+    static constexpr int LOGTV = (11 - LOGR) < 3 ? (11 - LOGR) : 3;
+};
 
 // One CTA iteration without pipelining (used by the persistent uneven-batch
 // kernel, whose next item may depend on this one).
-template <typename W, int DIR, int VAR, int LOGR, bool ROW>
-__device__ __forceinline__ void process_tile(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
-    const Geo<W, LOGR, ROW> geo(a);
-    const LaneTw<W> lt = load_lane_tw(a.tw);
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
+__device__ __forceinline__ void process_tile_tv(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
+    const Geo<W, LOGR, ROW, TVC> geo(a);
     tile_copy<W, LOGR, ROW, false>(a, geo, tile, buf);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    tile_rounds<W, DIR, VAR, LOGR, ROW>(a, geo, tile, buf, lt);
+    tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, buf);
     __syncthreads();
-    if (!Geo<W, LOGR, ROW>::DIRECT_STORE(DIR)) {
+    if (!Geo<W, LOGR, ROW, TVC>::DIRECT_STORE(DIR)) {
         tile_copy<W, LOGR, ROW, true>(a, geo, tile, buf);
         __syncthreads();
     }
 }
 
-// One pass over a batch: persistent CTAs with cp.async double buffering.
+// Column tiles of the widest default width only (the uneven-batch planner
+// guarantees it), so that one tile body is instantiated per (R, direction).
 template <typename W, int DIR, int VAR, int LOGR, bool ROW>
-__global__ void __launch_bounds__(kThreads, ROW ? 2 : 3) k_pass(const PassArgs<W> a) {
-    extern __shared__ uint4 sm[];
-    const Geo<W, LOGR, ROW> geo(a);
-    const LaneTw<W> lt = load_lane_tw(a.tw);
+__device__ __forceinline__ void process_tile(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
+    process_tile_tv<W, DIR, VAR, LOGR, ROW, ROW ? 0 : ColWidth<LOGR>::LOGTV>(a, tile, buf);
+}
+
+// One pass over a batch: persistent CTAs with cp.async double buffering.
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
+__device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
+    const Geo<W, LOGR, ROW, TVC> geo(a);
     uint32_t tile = blockIdx.x;
     if (tile < a.ntiles) tile_copy<W, LOGR, ROW, false>(a, geo, tile, sm);
     cp_async_commit();
@@ -539,14 +604,24 @@ __global__ void __launch_bounds__(kThreads, ROW ? 2 : 3) k_pass(const PassArgs<W
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        tile_rounds<W, DIR, VAR, LOGR, ROW>(a, geo, tile, cur, lt);
+        tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, cur);
         __syncthreads();
-        if (!Geo<W, LOGR, ROW>::DIRECT_STORE(DIR)) {
+        if (!Geo<W, LOGR, ROW, TVC>::DIRECT_STORE(DIR)) {
             tile_copy<W, LOGR, ROW, true>(a, geo, tile, cur);
             __syncthreads();
         }
     }
     cp_async_wait<0>();
+}
+
+template <typename W, int DIR, int VAR, int LOGR, bool ROW>
+__global__ void __launch_bounds__(kThreads, sizeof(W) == 4 ? 3 : 2) k_pass(const PassArgs<W> a) {
+    extern __shared__ uint4 sm[];
+    constexpr int TVF = ColWidth<LOGR>::LOGTV;
+    if (ROW || a.logTV == TVF)
+        pass_loop<W, DIR, VAR, LOGR, ROW, ROW ? 0 : TVF>(a, sm);
+    else
+        pass_loop<W, DIR, VAR, LOGR, ROW, -1>(a, sm);
 }
 
 // ---------------------------------------------------------------------------

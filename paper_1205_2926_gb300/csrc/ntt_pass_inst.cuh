@@ -99,13 +99,10 @@ static cudaError_t launch_kind(const LaunchSpec &s, int kind, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename W>
-static cudaError_t launch_pass_t(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st) {
-    if (dir == DIR_FWD)
-        return var == VAR_LAZY ? launch_kind<W, DIR_FWD, VAR_LAZY>(s, kind, st)
-                               : launch_kind<W, DIR_FWD, VAR_NTL>(s, kind, st);
-    return var == VAR_LAZY ? launch_kind<W, DIR_INV, VAR_LAZY>(s, kind, st)
-                           : launch_kind<W, DIR_INV, VAR_NTL>(s, kind, st);
+// Launch for one direction (instantiated in its own translation unit).
+template <typename W, int DIR>
+static cudaError_t launch_pass_dir(const LaunchSpec &s, int kind, int var, cudaStream_t st) {
+    return var == VAR_LAZY ? launch_kind<W, DIR, VAR_LAZY>(s, kind, st) : launch_kind<W, DIR, VAR_NTL>(s, kind, st);
 }
 
 }  // namespace ntt

@@ -1,8 +1,11 @@
-// Pass kernels for 32-bit words (beta = 2^32, p < 2^30).
-#include "ntt_pass_inst.cuh"
+// Dispatch of the pass kernels for 32-bit words to the per-direction units.
+#include "ntt_internal.hpp"
 
 namespace ntt {
+cudaError_t launch_pass_u32_fwd(const LaunchSpec &s, int kind, int var, cudaStream_t st);
+cudaError_t launch_pass_u32_inv(const LaunchSpec &s, int kind, int var, cudaStream_t st);
+
 cudaError_t launch_pass_u32(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st) {
-    return launch_pass_t<uint32_t>(s, kind, dir, var, st);
+    return dir == 0 ? launch_pass_u32_fwd(s, kind, var, st) : launch_pass_u32_inv(s, kind, var, st);
 }
 }  // namespace ntt

@@ -84,15 +84,16 @@ uint32_t bitrev(uint32_t k, int bits) {
 
 static int ilog2u(uint64_t x) { return 63 - __builtin_clzll(x); }
 
-// Default split of log L into passes: one row pass of at most 2^12 elements,
-// preceded by as few column passes (each at most 2^10) as needed, balanced.
+// Default split of log L into passes: one row pass of at most 2^11
+// elements, preceded by as few column passes (each at most 2^11) as needed,
+// balanced.
 static int default_split(int logL, int wbytes, int *logr) {
     (void)wbytes;
     if (logL <= kMaxRowLog) {
         logr[0] = logL;
         return 1;
     }
-    if (logL <= 22) {
+    if (logL <= 2 * kMaxRowLog) {
         int c = std::max(logL - kMaxRowLog, std::min((logL + 1) / 2, 9));
         logr[0] = c;
         logr[1] = logL - c;
@@ -105,13 +106,13 @@ static int default_split(int logL, int wbytes, int *logr) {
     return 3;
 }
 
-static bool split_ok(int logL, int wbytes, int n, const int *logr) {
+bool split_allowed(int logL, int wbytes, int n, const int *logr) {
     if (n < 1 || n > kMaxPasses) return false;
     if (logL <= 2) return n == 1 && logr[0] == logL;
     int sum = 0;
     const int logT = wbytes == 4 ? 5 : 4;  // narrowest column tile is 16 bytes; need S >= 8 vectors
     for (int i = 0; i < n; ++i) {
-        if (logr[i] < 3 || logr[i] > kMaxRowLog) return false;
+        if (logr[i] < 3 || logr[i] > std::max(kMaxRowLog, kMaxColLog)) return false;
         sum += logr[i];
     }
     if (sum != logL) return false;
@@ -318,15 +319,14 @@ void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s) {
     const PassPlan &ps = pl->pass[q];
     const int logV = pl->wbytes == 4 ? 2 : 1;
     const int logR = ps.logR;
-    if (q == pl->npass - 1) {  // row pass: vectors of V consecutive elements
-        const int logS = logR - logV;
-        const int le = std::min(3, logS);
-        const uint32_t units_per_row = 1u << (logS - le);
-        const uint32_t ns = 1u << logS, nsp = ns + (ns >> 3);
+    if (q == pl->npass - 1) {  // row pass: groups of V rows, one per vector lane
+        const uint32_t units_per_group = (1u << logR) >> 3;
+        const uint32_t nsp = (1u << logR) + ((1u << logR) >> 3);
         s.logTV = 0;
-        s.per_cta = (int)std::max<uint32_t>(1, kThreads / units_per_row);
+        s.per_cta = (int)std::max<uint32_t>(1, kThreads / units_per_group);
         s.nrows = s.nrows ? s.nrows : (batch << (pl->logL - logR));
-        s.ntiles = (uint32_t)((s.nrows + s.per_cta - 1) / s.per_cta);
+        const uint64_t rows_per_iter = (uint64_t)s.per_cta << logV;
+        s.ntiles = (uint32_t)((s.nrows + rows_per_iter - 1) / rows_per_iter);
         s.buf_chunks = (uint32_t)s.per_cta * nsp;
     } else {  // column pass: R rows x TV vectors per sub-tile
         int logTV = std::min(ps.logTV, std::max(0, 11 - logR));  // R * TV <= 2048 vectors per buffer
@@ -467,7 +467,7 @@ int ntt_plan_get_info(ntt_plan_t pl, ntt_plan_info_t *info) {
 
 int ntt_plan_set_split(ntt_plan_t pl, int n_passes, const int *log_r) {
     if (!pl || !log_r) return NTT_ERR_ARG;
-    if (!split_ok(pl->logL, pl->wbytes, n_passes, log_r)) return NTT_ERR_ARG;
+    if (!split_allowed(pl->logL, pl->wbytes, n_passes, log_r)) return NTT_ERR_ARG;
     cudaDeviceSynchronize();
     return apply_split(pl, n_passes, log_r);
 }

@@ -215,7 +215,17 @@ static UStage make_stage(const ntt_plan_s *pl, int dir, int i, uint32_t nrows_cl
     LaunchSpec s;
     memset(&s, 0, sizeof(s));
     s.nrows = nrows_class;
-    tile_params(pl, q, 1, s);
+    // a large batch count: no tile narrowing (the batch itself fills the GPU)
+    tile_params(pl, q, 1u << 20, s);
+    s.nrows = nrows_class ? nrows_class : (1ull << (pl->logL - ps.logR));
+    s.ntiles = (uint32_t)((s.nrows + ((uint64_t)s.per_cta << 2) - 1) / ((uint64_t)s.per_cta << 2));
+    if (q != n - 1) {
+        const int logV = 2;
+        const uint64_t sub = 1ull << (pl->logL - ps.logR - s.logTV - logV);
+        s.ntiles = (uint32_t)((sub + s.per_cta - 1) / s.per_cta);
+        // the persistent kernel carries column tiles of the default width only
+        if (s.logTV != std::min(3, 11 - ps.logR)) *smem = (size_t)-1;
+    }
     UStage sg;
     memset(&sg, 0, sizeof(sg));
     sg.logR = (int8_t)ps.logR;
@@ -232,7 +242,7 @@ static UStage make_stage(const ntt_plan_s *pl, int dir, int i, uint32_t nrows_cl
         sg.ma = (const uint32_t *)ps.ma[dir];
         sg.mb = (const uint32_t *)ps.mb[dir];
     }
-    *smem = std::max(*smem, (size_t)s.buf_chunks * 16);
+    if (*smem != (size_t)-1) *smem = std::max(*smem, (size_t)s.buf_chunks * 16);
     return sg;
 }
 
@@ -302,6 +312,7 @@ static int prepare(const ntt_desc_t *descs, size_t n, Prepared &pr) {
             }
         }
     }
+    if (smem == (size_t)-1) return NTT_ERR_RANGE;  // a plan with a narrow column tile
     // items: stage 0 of multi-pass tasks, class tasks, then later stages
     std::vector<UItem> items;
     for (size_t ti = 0; ti < tasks.size(); ++ti)

@@ -1,0 +1,114 @@
+// butterfly_rate.cu -- register-only throughput of the library's butterflies
+// on the current GPU (the integer-pipe roof used by bench.py).
+//
+// Each thread keeps 8 vectors of 4 residues in registers and runs rounds of
+// three radix-2 stages (12 butterflies per lane) with twiddles held in
+// registers, so no memory traffic limits the rate.  Reported: butterflies
+// per clock per SM at the GPU's maximum clock, per butterfly form, and the
+// raw rates of mul.hi.u32 and mad.lo.u32 chains.  out[] (grid*block words)
+// receives an xor of each thread's data so nothing is optimised away.
+// Built and run by `python bench.py --workload probe`.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../modarith.cuh"
+
+using namespace ntt;
+
+template <int F>
+__device__ __forceinline__ void bf(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wq, uint32_t p, uint32_t p2) {
+    if (F == 0) bfly_fwd_lazy(x, y, w, wq, p, p2);
+    if (F == 1) bfly_fwd_ntl(x, y, w, wq, p);
+    if (F == 2) bfly_inv_lazy(x, y, w, wq, p, p2);
+    if (F == 3) bfly_inv_ntl(x, y, w, wq, p);
+    if (F == 4) bfly_fwd_lazy_w1(x, y, p2);
+}
+
+template <int F>
+__global__ void k_rate(uint32_t *out, int iters, uint32_t p, uint32_t w0, uint32_t wq0) {
+    uint32_t x[8][4];
+    for (int j = 0; j < 8; ++j)
+        for (int v = 0; v < 4; ++v) x[j][v] = (threadIdx.x * 37u + j * 11u + v) % p;
+    uint32_t w[7], wq[7];
+    for (int i = 0; i < 7; ++i) {
+        w[i] = w0 + i;
+        wq[i] = wq0 + i;
+    }
+    const uint32_t p2 = 2 * p;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int lb = 2; lb >= 0; --lb)
+#pragma unroll
+            for (int jl = 0; jl < (1 << lb); ++jl)
+#pragma unroll
+                for (int jh = 0; jh < 8; jh += (2 << lb))
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        bf<F>(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w[(1 << lb) - 1 + jl], wq[(1 << lb) - 1 + jl],
+                              p, p2);
+    }
+    uint32_t s = 0;
+    for (int j = 0; j < 8; ++j)
+        for (int v = 0; v < 4; ++v) s ^= x[j][v];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int OP>
+__global__ void k_mul(uint32_t *out, int iters, uint32_t seed) {
+    uint32_t a[8], b = seed * 2654435761u + threadIdx.x;
+    for (int i = 0; i < 8; ++i) a[i] = b + i * 977u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = OP == 0 ? __umulhi(a[i], b) ^ i : a[i] * b + 0x9E3779B9u;
+    }
+    uint32_t s = 0;
+    for (int i = 0; i < 8; ++i) s ^= a[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename K, typename... A>
+static double timed(K k, int grid, int block, A... args) {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k<<<grid, block>>>(args...);
+    cudaEventRecord(e0);
+    k<<<grid, block>>>(args...);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+int main() {
+    int dev = 0, sms = 0, clk_khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    const int grid = sms * 4, block = 256, iters = 256;
+    uint32_t *out = nullptr;
+    if (cudaMalloc(&out, (size_t)grid * block * sizeof(uint32_t)) != cudaSuccess) return 1;
+    const uint32_t p = 998244353u, w0 = 12345u, wq0 = (uint32_t)(((uint64_t)w0 << 32) / p);
+    const double clk = clk_khz * 1e3, bf = 48.0 * iters * (double)grid * block;
+    const char *names[5] = {"lazy_fwd", "ntl_fwd", "lazy_inv", "ntl_inv", "lazy_fwd_w1"};
+    double ms[5];
+    ms[0] = timed(k_rate<0>, grid, block, out, iters, p, w0, wq0);
+    ms[1] = timed(k_rate<1>, grid, block, out, iters, p, w0, wq0);
+    ms[2] = timed(k_rate<2>, grid, block, out, iters, p, w0, wq0);
+    ms[3] = timed(k_rate<3>, grid, block, out, iters, p, w0, wq0);
+    ms[4] = timed(k_rate<4>, grid, block, out, iters, p, w0, wq0);
+    printf("{\"sms\": %d, \"max_clock_mhz\": %.0f", sms, clk / 1e6);
+    for (int i = 0; i < 5; ++i)
+        printf(", \"%s_bfly_per_clk_sm\": %.3f", names[i], bf / (ms[i] * 1e-3) / clk / sms);
+    const double mops = 8.0 * 4096 * (double)grid * block;
+    const double t_hi = timed(k_mul<0>, grid, block, out, 4096, 1u), t_lo = timed(k_mul<1>, grid, block, out, 4096, 1u);
+    printf(", \"mulhi_per_clk_sm\": %.2f, \"madlo_per_clk_sm\": %.2f", mops / (t_hi * 1e-3) / clk / sms,
+           mops / (t_lo * 1e-3) / clk / sms);
+    printf(", \"error\": \"%s\"}\n", cudaGetErrorString(cudaGetLastError()));
+    cudaFree(out);
+    return 0;
+}

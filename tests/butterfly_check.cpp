@@ -74,10 +74,34 @@ static void check_one(const Consts<W> &c, uint64_t X, uint64_t Y, uint64_t p, in
             ey = mulmod(w, (X % p + p - Y % p) % p, p);
             lim = 2 * p;
             break;
-        default:  // fully reduced inverse: [0,p) -> [0,p)
+        case 6:  // fully reduced inverse: [0,p) -> [0,p)
             bfly_inv_ntl(x, y, c.w, c.wq, c.p);
             ex = (X + mulmod(w, Y, p)) % p;
             ey = (X + p - mulmod(w, Y, p)) % p;
+            lim = p;
+            break;
+        case 13:  // W = 1 forms (only called with w == 1)
+            bfly_fwd_lazy_w1(x, y, c.p2);
+            ex = (X + Y) % p;
+            ey = (X % p + p - Y % p) % p;
+            lim = 2 * p;
+            break;
+        case 12:
+            bfly_fwd_ntl_w1(x, y, c.p);
+            ex = (X + Y) % p;
+            ey = (X + p - Y) % p;
+            lim = p;
+            break;
+        case 14:
+            bfly_inv_lazy_w1(x, y, c.p2);
+            ex = (X % p + Y % p) % p;
+            ey = (X % p + p - Y % p) % p;
+            lim = 4 * p;
+            break;
+        default:  // 16: fully reduced inverse with W = 1
+            bfly_inv_ntl_w1(x, y, c.p);
+            ex = (X + Y) % p;
+            ey = (X + p - Y) % p;
             lim = p;
             break;
     }
@@ -93,7 +117,7 @@ static void check_one(const Consts<W> &c, uint64_t X, uint64_t Y, uint64_t p, in
 }
 
 static uint64_t in_limit(int which, uint64_t p) {
-    return which == 3 || which == 5 ? 2 * p : which == 4 ? 4 * p : p;
+    return which == 3 || which == 5 || which == 13 ? 2 * p : which == 4 || which == 14 ? 4 * p : p;
 }
 
 // Exhaustive at beta = 2^8.
@@ -101,10 +125,10 @@ static long long exhaustive8() {
     long long n = 0;
     for (uint64_t p = 3; p < 128; p++) {
         if (!isprime_u64(p)) continue;
-        for (int which : {2, 3, 4, 5, 6}) {
-            bool lazy = which == 3 || which == 4 || which == 5;
+        for (int which : {2, 3, 4, 5, 6, 12, 13, 14, 16}) {
+            bool lazy = which == 3 || which == 4 || which == 5 || which == 13 || which == 14;
             if (lazy && p >= 64) continue;  // p < beta/4 (Algorithms 3-5)
-            for (uint64_t w = 1; w < p; w++) {
+            for (uint64_t w = 1; w < (which >= 12 ? 2 : p); w++) {
                 Consts<uint8_t> c = make<uint8_t>(p, w, 8);
                 uint64_t lim = in_limit(which, p);
                 for (uint64_t X = 0; X < lim; X++)
@@ -126,11 +150,12 @@ static uint64_t rnd() {
 template <typename W>
 static long long sampled(uint64_t p, int bits, int samples) {
     long long n = 0;
-    for (int which : {2, 3, 4, 5, 6}) {
+    for (int which : {2, 3, 4, 5, 6, 12, 13, 14, 16}) {
         uint64_t lim = in_limit(which, p);
         for (int s = 0; s < samples; s++) {
             uint64_t w = 1 + rnd() % (p - 1);
             if (s < 4) w = s < 2 ? 1 + s : p - 1 - (s - 2);
+            if (which >= 12) w = 1;
             Consts<W> c = make<W>(p, w, bits);
             uint64_t edge[6] = {0, 1, p - 1, p % lim, lim - 1, lim - 2};
             for (int t = 0; t < 64; t++) {

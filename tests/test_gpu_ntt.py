@@ -99,7 +99,8 @@ def test_redundant_inputs(p, logL):
 SPLITS = {
     11: [[11], [3, 8], [6, 5], [3, 3, 5]],
     14: [[7, 7], [3, 11], [9, 5], [4, 4, 6], [3, 3, 3, 5], [10, 4]],
-    17: [[5, 12], [9, 8], [10, 7], [4, 5, 8], [6, 6, 5]],
+    17: [[5, 12], [9, 8], [10, 7], [6, 11], [11, 6], [4, 5, 8], [6, 6, 5]],
+    22: [[11, 11], [10, 12], [6, 5, 11]],
 }
 
 
@@ -113,7 +114,8 @@ def test_every_split(p, logL, split, variant):
     w = o.root_of_unity(p, L)
     plan = ntt.ntt_plan(p, w, L)
     min_after = 5 if plan.word_bytes == 4 else 4  # a column pass needs >= 128 bytes per tile row
-    valid = all(logL - sum(split[:i + 1]) >= min_after for i in range(len(split) - 1))
+    valid = all(logL - sum(split[:i + 1]) >= min_after for i in range(len(split) - 1)) and \
+        all(3 <= r <= 11 for r in split)
     if not valid:
         with pytest.raises(ntt.NTTError) as e:
             plan.set_split(split)
@@ -221,7 +223,7 @@ def test_argument_errors():
     with pytest.raises(ntt.NTTError) as e:
         ntt.ntt_forward_batch(plan, d, 0)
     assert e.value.code == -4
-    for bad in ([5, 4], [2, 8], [11, 3], [3, 3, 2, 2]):  # wrong sum / pass too short / too long / tail < 2^5
+    for bad in ([5, 4], [2, 8], [11, 3], [3, 3, 2, 2], [4, 2, 4]):  # wrong sum / too short / tail < 2^5
         with pytest.raises(ntt.NTTError) as e:
             plan.set_split(bad)
         assert e.value.code == -4
