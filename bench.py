@@ -209,6 +209,22 @@ def barrier(dist):
         dist.barrier()
 
 
+def reduce_max(x: float, dist, device: str) -> float:
+    """Max of a per-rank value over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput of independent replicas: all ranks' units over the
+    slowest rank's time (weak scaling, no data-path collective)."""
+    return units_per_rank * world / max_seconds
+
+
 def capture_step(wl, torch):
     """CUDA graph of one step (forward + inverse of every group on its own
     stream, forked from and joined back to the capturing stream)."""
@@ -282,11 +298,7 @@ def kernel_stats(events, groups):
 
 
 def max_over_ranks(x, dist, torch):
-    if dist is None or not dist.is_initialized():
-        return x
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return reduce_max(x, dist, "cuda")
 
 
 def cpu_sample(groups, budget_s):
@@ -512,8 +524,8 @@ def run_ours(args, dist, rank, world):
     ms_e2e = max_over_ranks(ms_e2e, dist, torch)
 
     K = args.steps
-    value = world * bfly_step * K / (ms_lazy / 1e3)
-    ntl_value = world * bfly_step * K / (ms_ntl / 1e3)
+    value = job_value(bfly_step * K, world, ms_lazy / 1e3)
+    ntl_value = job_value(bfly_step * K, world, ms_ntl / 1e3)
     ds = stats[dom]
     gi, inv, k = dom
     p_, l_, b_ = groups[gi]
