@@ -153,10 +153,17 @@ int ntt_inverse_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride
 int ntt_execute_step(ntt_plan_t plan, int inverse, int step, void *d_data, size_t batch, size_t stride_words,
                      void *stream);
 
-/* Same transforms on HOST buffers: copies the batch to a device buffer owned
- * by the plan (grown on demand), transforms it on `stream`, copies it back
- * and synchronises the stream before returning.  `inverse` is 0 or 1.  For
+/* Same transforms on HOST buffers (Algorithm 1 / its inverse as above).
+ * h_data holds batch*stride_words words.  The batch is copied to a device
+ * buffer owned by the plan (grown on demand), transformed on `stream`, and
+ * copied back; the call returns after `stream` has finished.  A batch of
+ * several transforms is cut into chunks of whole transforms (at most 16,
+ * about 2 MiB each) so that copy-in, transform and copy-out of different
+ * chunks overlap on the plan's two copy streams.  Work queued earlier on
+ * `stream` completes before the first copy.  `inverse` is 0 or 1.  With
  * pinned host memory the copies are asynchronous DMA; any host memory works.
+ * Calls on one plan serialise (a plan mutex); calls on different plans from
+ * different threads run concurrently.
  * Errors: as above plus NTT_ERR_NOMEM. */
 int ntt_transform_host(ntt_plan_t plan, int inverse, void *h_data, size_t batch, size_t stride_words,
                        void *stream);

@@ -95,8 +95,8 @@ NTT_HD void bfly_fwd_ntl(W &x, W &y, W w, W wq, W p) {
 }
 
 // x - c if x >= c else x, written as a compare and select (same result as
-// csub for 0 <= x < 2c); on sm_103a this form schedules better in the
-// butterfly than the unsigned minimum.
+// csub for 0 <= x < 2c).  The compiler schedules the product-free W = 1
+// butterfly better with this form; the general butterflies use csub.
 template <typename W>
 NTT_HD W csub_sel(W x, W c) {
     return x >= c ? (W)(x - c) : x;
@@ -107,7 +107,7 @@ NTT_HD W csub_sel(W x, W c) {
 // Y' = W T - Q p in [0, 2p) without the final correction.
 template <typename W>
 NTT_HD void bfly_fwd_lazy(W &x, W &y, W w, W wq, W p, W p2) {
-    W s = csub_sel((W)(x + y), p2);
+    W s = csub((W)(x + y), p2);
     W t = (W)(x - y + p2);
     y = shoup_mul(t, w, wq, p);
     x = s;

@@ -49,9 +49,13 @@ struct ntt_plan_s {
     void *tw[2] = {nullptr, nullptr};  // stage tables per direction
     int tw_log = 0;                    // tables cover distances m < 2^tw_log
     uint64_t table_bytes = 0;
-    // host-buffer staging (ntt_transform_host)
+    // host-buffer staging (ntt_transform_host): a device copy of the batch,
+    // and the copy-in / copy-out streams and events of its chunk pipeline
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t hs_in = nullptr, hs_out = nullptr;
+    cudaEvent_t hev_start = nullptr, hev_end = nullptr;
+    cudaEvent_t hev_in[16] = {}, hev_done[16] = {};
     std::mutex mu;
 };
 
@@ -92,6 +96,9 @@ int enqueue_steps(ntt_plan_s *plan, int dir, void *data, size_t batch, size_t st
 
 // Whether a pass split is allowed for a transform of 2^logL words of wbytes.
 bool split_allowed(int logL, int wbytes, int n, const int *logr);
+
+// Free the staging buffer, streams and events of ntt_transform_host.
+void release_host_pipeline(ntt_plan_s *plan);
 
 // Record a CUDA failure for ntt_last_cuda_error(); returns NTT_ERR_CUDA.
 int cuda_fail(cudaError_t e, const char *where);

@@ -27,8 +27,11 @@
 // twiddle:
 //   column pass: lanes are V adjacent columns (one 16-byte global chunk);
 //   row pass: lanes are V consecutive rows; the copy into shared memory
-//     transposes (one word per cp.async), and the forward pass's last round
-//     writes eight consecutive words of each row straight to HBM.
+//     transposes (one word per cp.async).
+// The last round of every pass writes straight from registers to HBM:
+// 16-byte vectors in a column pass, eight consecutive words of each row in
+// the forward row pass, and in the inverse row pass word stores in which
+// neighbouring threads write neighbouring words of a row.
 // Each thread holds E = 8 vectors in registers and runs up to three
 // butterfly stages per round (radix-8 blocks); rounds exchange vectors
 // through shared memory.  The vector of row s sits at chunk
@@ -359,11 +362,6 @@ struct Geo {
     static constexpr uint32_t NS = 1u << LOGS;                       // vectors per sub-transform
     static constexpr uint32_t NSP = NS + (NS >> 3);                  // with padding
     using S = Sched<LOGS>;
-    // The last round stores straight from registers where that is
-    // coalesced: always in a column pass (neighbouring threads hold
-    // neighbouring column vectors), and in the forward row pass (each thread
-    // holds eight consecutive elements of each of its rows).
-    __host__ __device__ static constexpr bool DIRECT_STORE(int dir) { return !ROW || dir == DIR_FWD; }
 
     int logTV_, ltb, lbt;
     uint32_t sub_total;  // column pass: sub-tiles in the pass
@@ -393,20 +391,19 @@ struct Geo {
     }
 };
 
-// Global <-> shared copies of one CTA iteration.  A load issues cp.async
-// copies (completed through commit/wait groups); a store reads shared memory
-// and writes 16-byte vectors.  Consecutive threads take consecutive 16-byte
-// chunks of a row, so both directions are coalesced; addresses advance by
-// constant strides from a per-thread base.
-template <typename W, int LOGR, bool ROW, bool STORE, int TVC>
+// Global -> shared copy of one CTA iteration, issued as cp.async copies
+// (completed through commit/wait groups).  Column pass: consecutive threads
+// take consecutive 16-byte chunks of a tile row (coalesced), addresses
+// advance by constant strides from a per-thread base.  Row pass: element s of
+// row v of group gi goes to word v of chunk s + s/8 of the group's region,
+// each 16-byte global chunk as V copies of one word (the transposition into
+// lanes happens in the copy).
+template <typename W, int LOGR, bool ROW, int TVC>
 __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
                                           uint4 *buf) {
     using G = Geo<W, LOGR, ROW, TVC>;
     constexpr int V = Lanes<W>::V;
     if (ROW) {
-        // element s of row v of group gi <-> word v of chunk s + s/8 of the
-        // group's region; each 16-byte global chunk moves as V copies of one
-        // word (the transposition into lanes happens in the copy)
         constexpr int LOGV = Lanes<W>::LOGV;
         constexpr uint32_t NCH = (1u << LOGR) >> LOGV;  // 16-byte chunks per row
         const uint64_t row0 = (uint64_t)tile * a.per_cta * V;
@@ -415,23 +412,12 @@ __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOG
             const uint32_t c = i & (NCH - 1), rv = i / NCH;
             const uint64_t row = row0 + rv;
             if (row >= a.nrows) continue;
-            W *g = geo.row_ptr(a, row) + c * V;
+            const W *g = geo.row_ptr(a, row) + c * V;
             W *base = reinterpret_cast<W *>(buf + (rv >> LOGV) * G::NSP) + (rv & (V - 1));
-            if (STORE) {
-                uint4 q;
-                W *pq = reinterpret_cast<W *>(&q);
 #pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    const uint32_t e = c * V + k;
-                    pq[k] = base[(e + (e >> 3)) * V];
-                }
-                *reinterpret_cast<uint4 *>(g) = q;
-            } else {
-#pragma unroll
-                for (int k = 0; k < V; ++k) {
-                    const uint32_t e = c * V + k;
-                    cp_async_word<W>(base + (e + (e >> 3)) * V, g + k);
-                }
+            for (int k = 0; k < V; ++k) {
+                const uint32_t e = c * V + k;
+                cp_async_word<W>(base + (e + (e >> 3)) * V, g + k);
             }
         }
     } else {
@@ -445,15 +431,12 @@ __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOG
             if (t >= geo.sub_total) break;
             uint32_t ct;
             uint32_t s = srow & ((1u << LOGR) - 1u);
-            W *g = geo.col_origin(a, t, ct) + s * S + cc * V;
+            const W *g = geo.col_origin(a, t, ct) + s * S + cc * V;
             uint4 *sp = buf + ((ti * G::NSP + s + (s >> 3)) << logTV) + cc;
             const uint64_t gstep = rows_step * S;
             const uint32_t sstep = (rows_step + rows_step / 8) << logTV;
             for (; s < (1u << LOGR); s += rows_step, srow += rows_step) {
-                if (STORE)
-                    *reinterpret_cast<uint4 *>(g) = *sp;
-                else
-                    cp_async16(sp, g);
+                cp_async16(sp, g);
                 g += gstep;
                 sp += sstep;
             }
@@ -461,10 +444,13 @@ __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOG
     }
 }
 
-// One round over the tile in shared memory (compile-time round index RI).
+// Butterflies of one unit (E vectors in registers) in round RI, then the
+// write-back: to shared memory, or, in the last round of a direct-store
+// pass, straight to global memory.
 template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC, int RI>
-__device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
-                                           uint4 *buf) {
+__device__ __forceinline__ void unit_round(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
+                                           uint4 *rp, uint32_t ti, uint32_t tv, uint32_t s0, uint32_t lo,
+                                           W (&x)[Geo<W, LOGR, ROW, TVC>::S::E][Lanes<W>::V]) {
     using G = Geo<W, LOGR, ROW, TVC>;
     using S = typename G::S;
     constexpr int V = Lanes<W>::V;
@@ -472,6 +458,84 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
     constexpr int B0 = S::b0(DIR, RI), NST = S::nst(DIR, RI);
     constexpr bool FIRST = RI == 0, LAST = RI == S::NR - 1;
     const W p = a.p, p2 = (W)(2 * a.p);
+    const int logTV = geo.logTV();
+    const bool mid = !ROW && (a.flags & F_MIDDLE) && ((DIR == DIR_INV && FIRST) || (DIR == DIR_FWD && LAST));
+    uint32_t c0 = 0;
+    if (mid) {
+        uint32_t ct;
+        geo.col_origin(a, tile * a.per_cta + ti, ct);
+        c0 = ((ct << logTV) + tv) * V;
+    }
+    // rounds holding the distance-1 stage (b0 = 0) of a column pass fuse
+    // it with the middle twiddle; every other round runs as is
+    constexpr bool FUSE = !ROW && B0 == 0 && LE == 3 && ((DIR == DIR_INV && FIRST) || (DIR == DIR_FWD && LAST));
+    if (FUSE && mid) {
+        if (DIR == DIR_INV) twiddle_and_first_stage<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+        round_regs<W, DIR, VAR, LE, B0, NST, true>(x, a.tw + 2 * lo, p, p2);
+        if (DIR == DIR_FWD) last_stage_and_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+    } else {
+        if (DIR == DIR_INV && FIRST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+        round_regs<W, DIR, VAR, LE, B0, NST>(x, a.tw + 2 * lo, p, p2);
+        if (DIR == DIR_FWD && LAST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
+    }
+    if (LAST && (a.flags & F_NORMALIZE)) normalize<W, DIR, VAR, E>(x, p, p2);
+    if (LAST) {
+        // the last round writes straight to global memory
+        if (ROW) {
+            const uint64_t row0 = ((uint64_t)tile * a.per_cta + ti) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (row0 + v < a.nrows) {
+                    W *gp = geo.row_ptr(a, row0 + v) + s0;
+                    if (B0 == 0) {
+                        // elements s0 .. s0+7 of the lane's row: 8 consecutive words
+#pragma unroll
+                        for (int q = 0; q < E; q += V) {
+                            uint4 c;
+                            W *pc = reinterpret_cast<W *>(&c);
+#pragma unroll
+                            for (int k = 0; k < V; ++k) pc[k] = x[q + k][v];
+                            *reinterpret_cast<uint4 *>(gp + q) = c;
+                        }
+                    } else {
+                        // element s0 + (j << b0): neighbouring threads hold
+                        // neighbouring elements, so each word store of a warp
+                        // covers consecutive words of the row
+#pragma unroll
+                        for (int j = 0; j < E; ++j) gp[j << B0] = x[j][v];
+                    }
+                }
+            }
+        } else {
+            const uint32_t t = tile * a.per_cta + ti;
+            if (t < geo.sub_total) {
+                uint32_t ct;
+                const uint64_t S = 1ull << a.logS;
+                W *gp = geo.col_origin(a, t, ct) + s0 * S + tv * V;
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    *reinterpret_cast<uint4 *>(gp + (uint64_t)(j << B0) * S) = pack<W>(x[j]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
+            rp[cj << logTV] = pack<W>(x[j]);
+        }
+    }
+}
+
+// One round over the tile in shared memory (compile-time round index RI).
+// A unit is E vectors of one sub-transform: s_j = hi | (j << b0) | lo.
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC, int RI>
+__device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
+                                           uint4 *buf) {
+    using G = Geo<W, LOGR, ROW, TVC>;
+    using S = typename G::S;
+    constexpr int V = Lanes<W>::V;
+    constexpr int LE = S::LE, E = S::E;
+    constexpr int B0 = S::b0(DIR, RI);
     const int logTV = geo.logTV();
     const uint32_t units = (uint32_t)a.per_cta << (G::LOGS - LE + logTV);
     for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
@@ -487,64 +551,7 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
             const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
             unpack(rp[cj << logTV], x[j]);
         }
-        const bool mid = !ROW && (a.flags & F_MIDDLE) && ((DIR == DIR_INV && FIRST) || (DIR == DIR_FWD && LAST));
-        uint32_t c0 = 0;
-        if (mid) {
-            uint32_t ct;
-            geo.col_origin(a, tile * a.per_cta + ti, ct);
-            c0 = ((ct << logTV) + tv) * V;
-        }
-        // rounds holding the distance-1 stage (b0 = 0) of a column pass fuse
-        // it with the middle twiddle; every other round runs as is
-        constexpr bool FUSE = !ROW && B0 == 0 && LE == 3 &&
-                              ((DIR == DIR_INV && FIRST) || (DIR == DIR_FWD && LAST));
-        if (FUSE && mid) {
-            if (DIR == DIR_INV) twiddle_and_first_stage<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
-            round_regs<W, DIR, VAR, LE, B0, NST, true>(x, a.tw + 2 * lo, p, p2);
-            if (DIR == DIR_FWD) last_stage_and_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
-        } else {
-            if (DIR == DIR_INV && FIRST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
-            round_regs<W, DIR, VAR, LE, B0, NST>(x, a.tw + 2 * lo, p, p2);
-            if (DIR == DIR_FWD && LAST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
-        }
-        if (LAST && (a.flags & F_NORMALIZE)) normalize<W, DIR, VAR, E>(x, p, p2);
-        if (LAST && G::DIRECT_STORE(DIR)) {
-            // last round writes straight to HBM (coalesced for this layout)
-            if (ROW) {
-                // b0 = 0: elements s0 .. s0+7 of each lane's row, 8 consecutive words
-                const uint64_t row0 = ((uint64_t)tile * a.per_cta + ti) * V;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (row0 + v < a.nrows) {
-                        W *gp = geo.row_ptr(a, row0 + v) + s0;
-#pragma unroll
-                        for (int q = 0; q < E; q += V) {
-                            uint4 c;
-                            W *pc = reinterpret_cast<W *>(&c);
-#pragma unroll
-                            for (int k = 0; k < V; ++k) pc[k] = x[q + k][v];
-                            *reinterpret_cast<uint4 *>(gp + q) = c;
-                        }
-                    }
-                }
-            } else {
-                const uint32_t t = tile * a.per_cta + ti;
-                if (t < geo.sub_total) {
-                    uint32_t ct;
-                    const uint64_t S = 1ull << a.logS;
-                    W *gp = geo.col_origin(a, t, ct) + s0 * S + tv * V;
-#pragma unroll
-                    for (int j = 0; j < E; ++j)
-                        *reinterpret_cast<uint4 *>(gp + (uint64_t)(j << B0) * S) = pack<W>(x[j]);
-                }
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
-                rp[cj << logTV] = pack<W>(x[j]);
-            }
-        }
+        unit_round<W, DIR, VAR, LOGR, ROW, TVC, RI>(a, geo, tile, rp, ti, tv, s0, lo, x);
     }
 }
 
@@ -570,16 +577,12 @@ struct ColWidth {
 template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
 __device__ __forceinline__ void process_tile_tv(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
     const Geo<W, LOGR, ROW, TVC> geo(a);
-    tile_copy<W, LOGR, ROW, false>(a, geo, tile, buf);
+    tile_copy<W, LOGR, ROW>(a, geo, tile, buf);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
     tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, buf);
     __syncthreads();
-    if (!Geo<W, LOGR, ROW, TVC>::DIRECT_STORE(DIR)) {
-        tile_copy<W, LOGR, ROW, true>(a, geo, tile, buf);
-        __syncthreads();
-    }
 }
 
 // Column tiles of the widest default width only (the uneven-batch planner
@@ -594,22 +597,18 @@ template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
 __device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
     const Geo<W, LOGR, ROW, TVC> geo(a);
     uint32_t tile = blockIdx.x;
-    if (tile < a.ntiles) tile_copy<W, LOGR, ROW, false>(a, geo, tile, sm);
+    if (tile < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, tile, sm);
     cp_async_commit();
     for (uint32_t it = 0; tile < a.ntiles; tile += gridDim.x, ++it) {
         uint4 *cur = (it & 1) ? sm + a.buf_chunks : sm;
         uint4 *nxt = (it & 1) ? sm : sm + a.buf_chunks;
         const uint32_t next = tile + gridDim.x;
-        if (next < a.ntiles) tile_copy<W, LOGR, ROW, false>(a, geo, next, nxt);
+        if (next < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, next, nxt);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, cur);
         __syncthreads();
-        if (!Geo<W, LOGR, ROW, TVC>::DIRECT_STORE(DIR)) {
-            tile_copy<W, LOGR, ROW, true>(a, geo, tile, cur);
-            __syncthreads();
-        }
     }
     cp_async_wait<0>();
 }

@@ -437,7 +437,7 @@ int ntt_plan_destroy(ntt_plan_t pl) {
     if (!pl) return NTT_ERR_ARG;
     cudaDeviceSynchronize();
     free_tables(pl);
-    if (pl->stage) cudaFree(pl->stage);
+    release_host_pipeline(pl);
     delete pl;
     return NTT_OK;
 }
@@ -499,33 +499,6 @@ int ntt_execute_step(ntt_plan_t pl, int inverse, int step, void *d_data, size_t 
     const int n = pl->logL <= 2 ? 1 : pl->npass;
     if ((inverse != 0 && inverse != 1) || step < 0 || step >= n) return NTT_ERR_ARG;
     return enqueue_steps(pl, inverse, d_data, batch, stride_words, (cudaStream_t)stream, step, 1);
-}
-
-int ntt_transform_host(ntt_plan_t pl, int inverse, void *h_data, size_t batch, size_t stride_words, void *stream) {
-    if (!pl || !h_data || batch == 0 || (inverse != 0 && inverse != 1)) return NTT_ERR_ARG;
-    if (stride_words < pl->L || ((stride_words * pl->wbytes) & 15)) return NTT_ERR_ALIGN;
-    std::lock_guard<std::mutex> lk(pl->mu);
-    const size_t bytes = batch * stride_words * pl->wbytes;
-    cudaStream_t st = (cudaStream_t)stream;
-    if (pl->stage_bytes < bytes) {
-        if (pl->stage) {
-            cudaStreamSynchronize(st);
-            cudaFree(pl->stage);
-        }
-        pl->stage = nullptr;
-        pl->stage_bytes = 0;
-        cudaError_t e = cudaMalloc(&pl->stage, bytes);
-        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "cudaMalloc");
-        pl->stage_bytes = bytes;
-    }
-    cudaError_t e = cudaMemcpyAsync(pl->stage, h_data, bytes, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "H2D");
-    int rc = enqueue_transform(pl, inverse, pl->stage, batch, stride_words, st);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(h_data, pl->stage, bytes, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return cuda_fail(e, "D2H");
-    e = cudaStreamSynchronize(st);
-    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "sync");
 }
 
 }  // extern "C"

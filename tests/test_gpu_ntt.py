@@ -193,6 +193,63 @@ def test_transform_host_roundtrip():
     assert np.array_equal(h.astype(np.uint64), (a.astype(object) * L % p).astype(np.uint64))
 
 
+@pytest.mark.parametrize("p,logL,batch,pad", [(P_NTT30, 15, 50, 4), (P_NTT62, 16, 9, 2), (P_NTT30, 11, 1100, 0)])
+def test_transform_host_chunked(p, logL, batch, pad):
+    """Batches above the chunk size go through the copy/transform pipeline in
+    uneven chunks; strided rows keep their padding words untouched."""
+    require_gpu()
+    L = 1 << logL
+    o = orc()
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    a = batch_inputs(710 + logL, batch, L, p)
+    h = np.zeros((batch, L + pad), dtype=a.dtype)
+    h[:, :L] = a
+    if pad:
+        h[:, L:] = 12345
+    ntt.ntt_transform_host(plan, False, h, batch, L + pad)
+    want = o.ntt_ref(p, w, a.astype(np.uint64))
+    assert np.array_equal(h[:, :L].astype(np.uint64), want)
+    if pad:
+        assert (h[:, L:] == 12345).all()
+    ntt.ntt_transform_host(plan, True, h, batch, L + pad)
+    assert np.array_equal(h[:, :L].astype(np.uint64), (a.astype(object) * L % p).astype(np.uint64))
+
+
+def test_transform_host_threads():
+    """Calls on different plans from different threads overlap and stay exact."""
+    torch = require_gpu()
+    import threading
+    o = orc()
+    jobs = []
+    for i, (p, logL, batch) in enumerate([(P_NTT30, 16, 24), (P_NTT30, 20, 1), (P_NTT62, 14, 40)]):
+        L = 1 << logL
+        w = o.root_of_unity(p, L)
+        a = batch_inputs(720 + i, batch, L, p)
+        jobs.append((ntt.ntt_plan(p, w, L), a, a.copy(), batch, torch.cuda.Stream(), p, w))
+    errs = []
+
+    def run(j):
+        plan, a, h, batch, s, p, w = j
+        try:
+            for _ in range(3):
+                ntt.ntt_transform_host(plan, False, h, batch, stream=s)
+                ntt.ntt_transform_host(plan, True, h, batch, stream=s)
+        except Exception as e:  # pragma: no cover - reported below
+            errs.append(e)
+
+    ts = [threading.Thread(target=run, args=(j,)) for j in jobs]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errs
+    for plan, a, h, batch, s, p, w in jobs:
+        # three round trips multiply by L^3 (unnormalised inverse)
+        want = (a.astype(object) * pow(plan.L, 3, p) % p).astype(np.uint64)
+        assert np.array_equal(h.astype(np.uint64), want)
+
+
 def test_argument_errors():
     torch = require_gpu()
     p = P_NTT30
