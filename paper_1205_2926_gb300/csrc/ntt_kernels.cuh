@@ -572,24 +572,23 @@ struct ColWidth {
     static constexpr int LOGTV = (11 - LOGR) < 3 ? (11 - LOGR) : 3;
 };
 
-// One CTA iteration without pipelining (used by the persistent uneven-batch
-// kernel, whose next item may depend on this one).
-template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
-__device__ __forceinline__ void process_tile_tv(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
+// The two halves of one CTA iteration, for the persistent uneven-batch kernel
+// (which pipelines them across its work items itself): issue the tile's
+// global -> shared copies, and run the tile's rounds once they have landed.
+// Column tiles have the widest default width only (the uneven-batch planner
+// guarantees it), so that one tile body is instantiated per (R, direction).
+template <typename W, int LOGR, bool ROW>
+__device__ __forceinline__ void tile_load(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
+    constexpr int TVC = ROW ? 0 : ColWidth<LOGR>::LOGTV;
     const Geo<W, LOGR, ROW, TVC> geo(a);
     tile_copy<W, LOGR, ROW>(a, geo, tile, buf);
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncthreads();
-    tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, buf);
-    __syncthreads();
 }
 
-// Column tiles of the widest default width only (the uneven-batch planner
-// guarantees it), so that one tile body is instantiated per (R, direction).
 template <typename W, int DIR, int VAR, int LOGR, bool ROW>
-__device__ __forceinline__ void process_tile(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
-    process_tile_tv<W, DIR, VAR, LOGR, ROW, ROW ? 0 : ColWidth<LOGR>::LOGTV>(a, tile, buf);
+__device__ __forceinline__ void tile_compute(const PassArgs<W> &a, uint32_t tile, uint4 *buf) {
+    constexpr int TVC = ROW ? 0 : ColWidth<LOGR>::LOGTV;
+    const Geo<W, LOGR, ROW, TVC> geo(a);
+    tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, buf);
 }
 
 // One pass over a batch: persistent CTAs with cp.async double buffering.

@@ -75,17 +75,21 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *(volatile const int *)p; }
 
-template <int DIR, bool ROW, int LO, int HI>
-__device__ __forceinline__ void run_logr(int logR, const PassArgs<uint32_t> &a, uint32_t tile, uint4 *sm) {
+// Run-time dispatch on log2 R of a stage: issue its tile copies (MODE 0),
+// or run its rounds (MODE 1).
+template <int MODE, int DIR, bool ROW, int LO, int HI>
+__device__ __forceinline__ void run_logr(int logR, const PassArgs<uint32_t> &a, uint32_t tile, uint4 *buf) {
     if (logR == LO) {
-        process_tile<uint32_t, DIR, VAR_LAZY, LO, ROW>(a, tile, sm);
+        if (MODE == 0)
+            tile_load<uint32_t, LO, ROW>(a, tile, buf);
+        else
+            tile_compute<uint32_t, DIR, VAR_LAZY, LO, ROW>(a, tile, buf);
         return;
     }
-    if constexpr (LO < HI) run_logr<DIR, ROW, LO + 1, HI>(logR, a, tile, sm);
+    if constexpr (LO < HI) run_logr<MODE, DIR, ROW, LO + 1, HI>(logR, a, tile, buf);
 }
 
-template <int DIR, bool ROW>
-__device__ __forceinline__ void run_item(const UTask &t, const UStage &sg, uint32_t cta, uint4 *sm) {
+__device__ __forceinline__ PassArgs<uint32_t> item_args(const UTask &t, const UStage &sg) {
     PassArgs<uint32_t> a;
     a.data = t.data;
     a.stride = 1ull << t.logL;
@@ -104,70 +108,147 @@ __device__ __forceinline__ void run_item(const UTask &t, const UStage &sg, uint3
     a.p = t.p;
     a.rowptrs = t.rowptrs;
     a.nrows = t.rowptrs ? t.nrows : (1ull << (t.logL - sg.logR));
-    if (ROW)
-        run_logr<DIR, true, 3, kMaxRowLog>(sg.logR, a, cta, sm);
-    else
-        run_logr<DIR, false, 3, kMaxColLog>(sg.logR, a, cta, sm);
+    return a;
 }
 
-__global__ void __launch_bounds__(kThreads) k_uneven(const UTask *__restrict__ tasks, const UItem *__restrict__ items,
-                                                      uint32_t n_items, unsigned int *done, UCtl *ctl,
-                                                      long long wait_budget, int stall_stage) {
+// Issue the copies (MODE 0) or run the rounds (MODE 1) of a work item.
+template <int MODE>
+__device__ __forceinline__ void run_item(const UTask &t, const UStage &sg, uint32_t cta, uint4 *buf) {
+    const PassArgs<uint32_t> a = item_args(t, sg);
+    if (t.dir == DIR_FWD) {
+        if (sg.row)
+            run_logr<MODE, DIR_FWD, true, 3, kMaxRowLog>(sg.logR, a, cta, buf);
+        else
+            run_logr<MODE, DIR_FWD, false, 3, kMaxColLog>(sg.logR, a, cta, buf);
+    } else {
+        if (sg.row)
+            run_logr<MODE, DIR_INV, true, 3, kMaxRowLog>(sg.logR, a, cta, buf);
+        else
+            run_logr<MODE, DIR_INV, false, 3, kMaxColLog>(sg.logR, a, cta, buf);
+    }
+}
+
+// Completions item `it` needs before its tile may be read: every CTA
+// iteration of the previous stage of its task.  A stall injected for testing
+// asks for one completion more than will ever happen, so that the bounded
+// wait must give up.
+__device__ __forceinline__ const unsigned int *dep_counter(const UTask &t, const UItem &item, int stall_stage,
+                                                           unsigned int *need, const unsigned int *done) {
+    if (item.stage == 0) return nullptr;
+    *need = t.st[item.stage - 1].units + (stall_stage == (int)item.stage ? 1u : 0u);
+    return done + t.done_base + item.stage - 1;
+}
+
+// Persistent kernel over a queue of work items in dependency order.  Each
+// CTA claims items with an atomic counter.  While it computes one item it
+// has already claimed the next and, when that item's dependencies are met at
+// claim time, copies its tile into the second shared buffer (cp.async double
+// buffering across items); otherwise it waits for them (bounded) after
+// finishing the current item.  Every item a CTA waits for was claimed
+// earlier and is processed before its owner blocks on a later one, so the
+// queue always drains.  A wait that runs out of its budget sets
+// NTT_ERR_TIMEOUT and the abort flag, and every CTA stops.
+__global__ void __launch_bounds__(kThreads, 3) k_uneven(const UTask *__restrict__ tasks,
+                                                         const UItem *__restrict__ items, uint32_t n_items,
+                                                         unsigned int *done, UCtl *ctl, long long wait_budget,
+                                                         int stall_stage, uint32_t buf_chunks) {
     extern __shared__ uint4 sm[];
     __shared__ unsigned int s_item;
-    __shared__ int s_skip;
-    for (;;) {
+    __shared__ int s_state;  // 1: dependencies met, 0: not yet, -1: stop
+    // claim an item; with `block`, wait (bounded) until its dependencies are met
+    auto claim = [&](bool block) -> unsigned int {
         if (threadIdx.x == 0) {
-            s_item = ld_volatile(&ctl->abort) ? n_items : atomicAdd(&ctl->next, 1u);
-            s_skip = 0;
+            const unsigned int it = ld_volatile(&ctl->abort) ? n_items : atomicAdd(&ctl->next, 1u);
+            s_item = it;
+            s_state = it >= n_items ? -1 : 1;
+            if (it < n_items) {
+                const UItem item = items[it];
+                unsigned int need = 0;
+                const unsigned int *cnt = dep_counter(tasks[item.task], item, stall_stage, &need, done);
+                if (cnt && ld_acquire(cnt) < need) s_state = 0;
+                if (s_state == 0 && block) {
+                    const long long t0 = clock64();
+                    while (ld_acquire(cnt) < need) {
+                        if (ld_volatile(&ctl->abort) || clock64() - t0 > wait_budget) break;
+                        __nanosleep(256);
+                    }
+                    if (ld_acquire(cnt) >= need) {
+                        s_state = 1;
+                    } else {
+                        if (!ld_volatile(&ctl->abort)) atomicExch(&ctl->status, NTT_ERR_TIMEOUT);
+                        atomicExch(&ctl->abort, 1);
+                        s_state = -1;
+                    }
+                }
+                __threadfence();
+            }
         }
         __syncthreads();
-        const unsigned int it = s_item;
-        if (it >= n_items) break;
-        const UItem item = items[it];
-        const UTask &t = tasks[item.task];
-        if (item.stage > 0 && threadIdx.x == 0) {
-            const UStage &prev = t.st[item.stage - 1];
-            // A stall injected for testing asks for one completion more than
-            // will ever happen, so that the bounded wait must give up.
-            const unsigned int need = prev.units + (stall_stage == (int)item.stage ? 1u : 0u);
-            const unsigned int *cnt = done + t.done_base + item.stage - 1;
-            const long long t0 = clock64();
-            while (ld_acquire(cnt) < need) {
-                if (ld_volatile(&ctl->abort)) {
-                    s_skip = 1;
-                    break;
+        return s_item;
+    };
+    // the same wait for an item claimed earlier
+    auto wait_ready = [&](unsigned int it) -> bool {
+        if (threadIdx.x == 0) {
+            const UItem item = items[it];
+            unsigned int need = 0;
+            const unsigned int *cnt = dep_counter(tasks[item.task], item, stall_stage, &need, done);
+            s_state = 1;
+            if (cnt) {
+                const long long t0 = clock64();
+                while (ld_acquire(cnt) < need) {
+                    if (ld_volatile(&ctl->abort) || clock64() - t0 > wait_budget) break;
+                    __nanosleep(256);
                 }
-                if (clock64() - t0 > wait_budget) {
-                    atomicExch(&ctl->status, NTT_ERR_TIMEOUT);
+                if (ld_acquire(cnt) < need) {
+                    if (!ld_volatile(&ctl->abort)) atomicExch(&ctl->status, NTT_ERR_TIMEOUT);
                     atomicExch(&ctl->abort, 1);
-                    s_skip = 1;
-                    break;
+                    s_state = -1;
                 }
-                __nanosleep(256);
             }
             __threadfence();
         }
         __syncthreads();
-        if (s_skip) break;
-        const UStage &sg = t.st[item.stage];
-        if (t.dir == DIR_FWD) {
-            if (sg.row)
-                run_item<DIR_FWD, true>(t, sg, item.cta, sm);
-            else
-                run_item<DIR_FWD, false>(t, sg, item.cta, sm);
-        } else {
-            if (sg.row)
-                run_item<DIR_INV, true>(t, sg, item.cta, sm);
-            else
-                run_item<DIR_INV, false>(t, sg, item.cta, sm);
+        return s_state == 1;
+    };
+    unsigned int cur = claim(true);
+    if (cur >= n_items || s_state != 1) return;
+    int b = 0;
+    {
+        const UItem item = items[cur];
+        run_item<0>(tasks[item.task], tasks[item.task].st[item.stage], item.cta, sm);
+    }
+    cp_async_commit();
+    for (;;) {
+        const unsigned int nxt = claim(false);
+        const bool have_next = nxt < n_items;
+        const bool prefetched = have_next && s_state == 1;
+        if (prefetched) {
+            const UItem item = items[nxt];
+            run_item<0>(tasks[item.task], tasks[item.task].st[item.stage], item.cta, sm + (b ^ 1) * buf_chunks);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        {
+            const UItem item = items[cur];
+            run_item<1>(tasks[item.task], tasks[item.task].st[item.stage], item.cta, sm + b * buf_chunks);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(done + t.done_base + item.stage, 1u);
+            atomicAdd(done + tasks[items[cur].task].done_base + items[cur].stage, 1u);
         }
+        if (!have_next) break;
+        if (!prefetched) {
+            if (!wait_ready(nxt)) break;
+            const UItem item = items[nxt];
+            run_item<0>(tasks[item.task], tasks[item.task].st[item.stage], item.cta, sm + (b ^ 1) * buf_chunks);
+            cp_async_commit();
+        }
+        cur = nxt;
+        b ^= 1;
     }
+    cp_async_wait<0>();
 }
 
 // ----------------------------------------------------------------- host side
@@ -181,6 +262,7 @@ struct Prepared {
     UCtl *d_ctl = nullptr;
     uint32_t n_items = 0, n_done = 0;
     size_t smem = 0;
+    uint32_t buf_chunks = 0;
     unsigned grid = 0;
     int device = -1;
     void release() {
@@ -353,7 +435,8 @@ static int prepare(const ntt_desc_t *descs, size_t n, Prepared &pr) {
     }
     pr.n_items = (uint32_t)items.size();
     pr.n_done = done;
-    pr.smem = std::max<size_t>(smem, 16);
+    pr.buf_chunks = (uint32_t)(std::max<size_t>(smem, 16) / 16);
+    pr.smem = (size_t)2 * pr.buf_chunks * 16;  // two tile buffers (pipelined items)
     // persistent grid: as many CTAs as fit on the device at once
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pr.device);
@@ -397,7 +480,7 @@ int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream) {
     if (e == cudaSuccess) e = cudaMemsetAsync(pr.d_ctl, 0, sizeof(UCtl), st);
     if (e != cudaSuccess) return cuda_fail(e, "uneven memset");
     k_uneven<<<pr.grid, kThreads, pr.smem, st>>>(pr.d_tasks, pr.d_items, pr.n_items, pr.d_done, pr.d_ctl,
-                                                  g_wait_budget, g_stall_stage);
+                                                  g_wait_budget, g_stall_stage, pr.buf_chunks);
     e = cudaGetLastError();
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "k_uneven");
 }
