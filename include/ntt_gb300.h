@@ -258,7 +258,8 @@ int ntt_uneven_set_wait_budget(long long cycles, int stall_stage);
  * requests in FIFO order while their device memory (2 L words each) fits in
  * mem_budget_bytes, groups them by L = nextpow2(na+nb-1), and runs each group
  * as one batch (forward transforms of both operands, pointwise product times
- * L^-1, inverse transform) on the next of n_streams CUDA streams.  Requests
+ * L^-1, inverse transform) on the one of n_streams CUDA streams with the
+ * least outstanding work (butterflies of its running batches).  Requests
  * arriving while batches run are admitted as memory frees up, and their
  * batches overlap with the running ones on the device.  Each result is the
  * same as polymul_mod_p on that request alone. */

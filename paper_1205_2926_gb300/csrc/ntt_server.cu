@@ -4,7 +4,9 @@
 // A scheduler thread owns the GPU work.  Submitted requests wait in a FIFO
 // queue; the scheduler admits them in order while their device memory fits
 // in the budget, groups the admitted ones by transform length L, and runs
-// each group as one batch on the next of several CUDA streams:
+// each group as one batch on the CUDA stream with the least outstanding work
+// (butterflies of the batches still running on it), so that small requests
+// do not queue behind a large one:
 //   zero the slab, copy operands in, forward transforms (2n vectors),
 //   pointwise product times L^-1, inverse transforms (n vectors), copy the
 //   na+nb-1 result words of each request straight to its host buffer.
@@ -62,6 +64,7 @@ struct Batch {
     cudaEvent_t done = nullptr;
     int stream = 0;
     int status = NTT_OK;
+    double work = 0;  // butterflies of the batch (stream load balancing)
 };
 
 }  // namespace ntt
@@ -71,7 +74,7 @@ struct ntt_server_s {
     int device = 0;
     size_t wbytes = 4;
     std::vector<cudaStream_t> streams;
-    int next_stream = 0;
+    std::vector<double> stream_work;  // outstanding butterflies per stream
     std::mutex mu;
     std::condition_variable cv, done_cv;
     std::deque<uint64_t> queue;
@@ -170,6 +173,7 @@ static void scheduler(ntt_server_s *sv) {
             if (q != cudaSuccess && q != cudaErrorNotReady) cudaGetLastError();
             for (uint64_t id : bt.ids) finish_request(sv, sv->reqs[id], st);
             sv->inflight_bytes -= bt.bytes;
+            sv->stream_work[bt.stream] -= bt.work;
             cudaEventDestroy(bt.done);
             sv->inflight.erase(sv->inflight.begin() + i);
             progressed = true;
@@ -194,8 +198,8 @@ static void scheduler(ntt_server_s *sv) {
             Batch bt;
             bt.ids = kv.second;
             bt.bytes = 2 * kv.first * sv->wbytes * bt.ids.size();
-            bt.stream = sv->next_stream;
-            sv->next_stream = (sv->next_stream + 1) % (int)sv->streams.size();
+            bt.work = (double)bfly_count(kv.first) * (double)bt.ids.size();
+            bt.stream = (int)(std::min_element(sv->stream_work.begin(), sv->stream_work.end()) - sv->stream_work.begin());
             cudaEventCreateWithFlags(&bt.done, cudaEventDisableTiming);
             std::vector<Request *> rs;
             for (uint64_t id : bt.ids) rs.push_back(&sv->reqs[id]);
@@ -220,6 +224,7 @@ static void scheduler(ntt_server_s *sv) {
             }
             sv->n_batches++;
             sv->inflight_bytes += bt.bytes;
+            sv->stream_work[bt.stream] += bt.work;
             sv->inflight.push_back(bt);
         }
         // 4. wait for work: short sleeps while batches run, block when idle
@@ -270,6 +275,7 @@ int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out) {
         }
         sv->streams.push_back(s);
     }
+    sv->stream_work.assign(sv->streams.size(), 0.0);
     sv->worker = std::thread(scheduler, sv);
     *out = sv;
     return NTT_OK;

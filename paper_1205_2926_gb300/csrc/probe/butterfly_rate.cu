@@ -67,6 +67,50 @@ __global__ void k_mul(uint32_t *out, int iters, uint32_t seed) {
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// 64-bit words: the lazy forward butterfly and the raw 64-bit multiplies
+// (mul.hi.u64 and mul.lo.u64, each built by the compiler from 32-bit
+// multiplies on this GPU).
+__global__ void k_rate64(uint64_t *out, int iters, uint64_t p, uint64_t w0, uint64_t wq0) {
+    uint64_t x[8][2];
+    for (int j = 0; j < 8; ++j)
+        for (int v = 0; v < 2; ++v) x[j][v] = (threadIdx.x * 37ull + j * 11ull + v) % p;
+    uint64_t w[7], wq[7];
+    for (int i = 0; i < 7; ++i) {
+        w[i] = w0 + i;
+        wq[i] = wq0 + i;
+    }
+    const uint64_t p2 = 2 * p;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int lb = 2; lb >= 0; --lb)
+#pragma unroll
+            for (int jl = 0; jl < (1 << lb); ++jl)
+#pragma unroll
+                for (int jh = 0; jh < 8; jh += (2 << lb))
+#pragma unroll
+                    for (int v = 0; v < 2; ++v)
+                        bfly_fwd_lazy(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w[(1 << lb) - 1 + jl],
+                                      wq[(1 << lb) - 1 + jl], p, p2);
+    }
+    uint64_t s = 0;
+    for (int j = 0; j < 8; ++j)
+        for (int v = 0; v < 2; ++v) s ^= x[j][v];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int OP>
+__global__ void k_mul64(uint64_t *out, int iters, uint64_t seed) {
+    uint64_t a[8], b = seed * 0x9E3779B97F4A7C15ull + threadIdx.x;
+    for (int i = 0; i < 8; ++i) a[i] = b + i * 977ull;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = OP == 0 ? __umul64hi(a[i], b) ^ i : a[i] * b + 0x9E3779B97F4A7C15ull;
+    }
+    uint64_t s = 0;
+    for (int i = 0; i < 8; ++i) s ^= a[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 template <typename K, typename... A>
 static double timed(K k, int grid, int block, A... args) {
     cudaEvent_t e0, e1;
@@ -108,6 +152,19 @@ int main() {
     const double t_hi = timed(k_mul<0>, grid, block, out, 4096, 1u), t_lo = timed(k_mul<1>, grid, block, out, 4096, 1u);
     printf(", \"mulhi_per_clk_sm\": %.2f, \"madlo_per_clk_sm\": %.2f", mops / (t_hi * 1e-3) / clk / sms,
            mops / (t_lo * 1e-3) / clk / sms);
+    uint64_t *out64 = nullptr;
+    if (cudaMalloc(&out64, (size_t)grid * block * sizeof(uint64_t)) == cudaSuccess) {
+        const uint64_t p64 = 2305843009448574977ull, w64 = 1234567ull;
+        const uint64_t wq64 = (uint64_t)(((unsigned __int128)w64 << 64) / p64);
+        const double bf64 = 24.0 * iters * (double)grid * block;
+        const double t64 = timed(k_rate64, grid, block, out64, iters, p64, w64, wq64);
+        const double mops64 = 8.0 * 1024 * (double)grid * block;
+        const double h64 = timed(k_mul64<0>, grid, block, out64, 1024, (uint64_t)1);
+        const double l64 = timed(k_mul64<1>, grid, block, out64, 1024, (uint64_t)1);
+        printf(", \"lazy_fwd_u64_bfly_per_clk_sm\": %.3f, \"mulhi_u64_per_clk_sm\": %.2f, \"mullo_u64_per_clk_sm\": %.2f",
+               bf64 / (t64 * 1e-3) / clk / sms, mops64 / (h64 * 1e-3) / clk / sms, mops64 / (l64 * 1e-3) / clk / sms);
+        cudaFree(out64);
+    }
     printf(", \"error\": \"%s\"}\n", cudaGetErrorString(cudaGetLastError()));
     cudaFree(out);
     return 0;
