@@ -115,12 +115,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# DRAM bytes (read + write) per launch of a pass kernel, from one ncu capture
+# of the current kernels (profiles/k_pass_u32_64x2p16_full.md), keyed by
+# workload and pass; passes without a capture report null.  The writes are 0:
+# the pass's output stays in the 129 MB L2 until it is evicted later.
+NCU_TRAFFIC = {
+    ("c2", "forward pass 0 of 64 x 2^16 (log2 R = 7)"): 17357568 + 0,
+    ("c2", "forward pass 1 of 64 x 2^16 (log2 R = 9)"): 16808960 + 0,
+    ("c2", "inverse pass 0 of 64 x 2^16 (log2 R = 9)"): 16814848 + 0,
+    ("c2", "inverse pass 1 of 64 x 2^16 (log2 R = 7)"): 17368064 + 0,
+}
+
+
 def alu_peak_bfly(word_bytes, sm_mhz):
-    """Integer-multiply roof in butterflies/s: per SM and clock, 32 mul.hi and
-    64 mad.lo (measured rates of this GB300), 1 + 2 of them per 32-bit lazy
-    butterfly (Section 5: three multiplies) -> 16 butterflies/clk/SM.  A
-    64-bit butterfly needs about 4x the 32-bit multiply work."""
-    per_clk = 16.0 if word_bytes == 4 else 4.0
+    """Integer-multiply roof in butterflies/s.  A butterfly takes one high and
+    two low products (Section 5: three multiplies); with the multiply rates
+    measured on this GB300 by `bench.py --workload probe` (per SM and clock:
+    mul.hi.u32 31.3, mad.lo.u32 62.8; mul.hi.u64 7.25, mul.lo.u64 15.1) that
+    is 1 / (1/hi + 2/lo) = 15.7 butterflies/clk/SM for 32-bit words and 3.7
+    for 64-bit words."""
+    per_clk = 1.0 / (1.0 / 31.3 + 2.0 / 62.8) if word_bytes == 4 else 1.0 / (1.0 / 7.25 + 2.0 / 15.1)
     return 152 * sm_mhz * 1e6 * per_clk
 
 
@@ -548,14 +562,16 @@ def run_ours(args, dist, rank, world):
     frac_hbm = achieved_gbs / peaks["hbm_gbs"]
     frac_alu = achieved_bfly / alu_peak
     dom_name = f"{'inverse' if inv else 'forward'} pass {k} of {b_} x 2^{l_} (log2 R = {log_r})"
+    traffic = NCU_TRAFFIC.get((args.workload, dom_name))
     if frac_alu >= frac_hbm:
         roof = {"bound": "alu", "achieved": achieved_bfly / 1e9, "peak": alu_peak / 1e9, "unit": "Gbutterflies/s",
-                "frac": frac_alu, "traffic": None, "kernel": dom_name,
-                "peak_src": "152 SMs x clock x 16 lazy butterflies/clk/SM (integer-multiply pipe)",
+                "frac": frac_alu, "traffic": traffic, "kernel": dom_name,
+                "peak_src": f"152 SMs x clock x {alu_peak / (152 * peaks['sm_max_mhz'] * 1e6):.0f} butterflies/clk/SM "
+                            "(measured multiply rates)",
                 "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": frac_hbm}}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": frac_hbm, "traffic": None, "kernel": dom_name, "peak_src": peaks["src"] + " (MEASURED_PEAKS.json)",
+                "frac": frac_hbm, "traffic": traffic, "kernel": dom_name, "peak_src": peaks["src"] + " (MEASURED_PEAKS.json)",
                 "alu": {"achieved": achieved_bfly / 1e9, "peak": alu_peak / 1e9, "unit": "Gbutterflies/s",
                         "frac": frac_alu}}
     line = {

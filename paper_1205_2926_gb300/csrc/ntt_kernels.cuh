@@ -97,14 +97,6 @@ __device__ __forceinline__ void cp_async16(uint4 *dst, const void *src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// Copy of one 4- or 8-byte word (the transposing row copies).
-template <typename W>
-__device__ __forceinline__ void cp_async_word(W *dst, const W *src) {
-    if (sizeof(W) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
@@ -391,35 +383,19 @@ struct Geo {
     }
 };
 
-// Global -> shared copy of one CTA iteration, issued as cp.async copies
-// (completed through commit/wait groups).  Column pass: consecutive threads
-// take consecutive 16-byte chunks of a tile row (coalesced), addresses
-// advance by constant strides from a per-thread base.  Row pass: element s of
-// row v of group gi goes to word v of chunk s + s/8 of the group's region,
-// each 16-byte global chunk as V copies of one word (the transposition into
-// lanes happens in the copy).
+// Global -> shared copy of one CTA iteration of a column pass, issued as
+// cp.async copies (completed through commit/wait groups): consecutive threads
+// take consecutive 16-byte chunks of a tile row (coalesced), addresses advance
+// by constant strides from a per-thread base.  A row pass has nothing to copy
+// ahead: its first round gathers the V rows of each lane vector straight from
+// global memory (tile_round).
 template <typename W, int LOGR, bool ROW, int TVC>
 __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
                                           uint4 *buf) {
     using G = Geo<W, LOGR, ROW, TVC>;
     constexpr int V = Lanes<W>::V;
     if (ROW) {
-        constexpr int LOGV = Lanes<W>::LOGV;
-        constexpr uint32_t NCH = (1u << LOGR) >> LOGV;  // 16-byte chunks per row
-        const uint64_t row0 = (uint64_t)tile * a.per_cta * V;
-        const uint32_t total = ((uint32_t)a.per_cta << LOGV) * NCH;
-        for (uint32_t i = threadIdx.x; i < total; i += kThreads) {
-            const uint32_t c = i & (NCH - 1), rv = i / NCH;
-            const uint64_t row = row0 + rv;
-            if (row >= a.nrows) continue;
-            const W *g = geo.row_ptr(a, row) + c * V;
-            W *base = reinterpret_cast<W *>(buf + (rv >> LOGV) * G::NSP) + (rv & (V - 1));
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                const uint32_t e = c * V + k;
-                cp_async_word<W>(base + (e + (e >> 3)) * V, g + k);
-            }
-        }
+        // row passes copy nothing ahead: their first round reads global memory
     } else {
         const int logTV = geo.logTV();
         const uint32_t cc = threadIdx.x & ((1u << logTV) - 1u);
@@ -538,6 +514,44 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
     constexpr int B0 = S::b0(DIR, RI);
     const int logTV = geo.logTV();
     const uint32_t units = (uint32_t)a.per_cta << (G::LOGS - LE + logTV);
+    if constexpr (ROW && RI == 0) {
+        // First round of a row pass: element s_j of each of the unit's V rows
+        // comes straight from global memory into lane j of the registers.
+        // Neighbouring threads take neighbouring elements (16-byte chunks when
+        // b0 = 0), so every warp load is coalesced; loads go through L2 only.
+        for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
+            const uint32_t g = u & ((G::NS >> LE) - 1u);
+            const uint32_t ti = u >> (G::LOGS - LE);
+            const uint32_t lo = g & ((1u << B0) - 1u);
+            const uint32_t s0 = ((g >> B0) << (B0 + LE)) | lo;
+            uint4 *rp = buf + ti * G::NSP + s0 + (s0 >> 3);
+            const uint64_t row0 = ((uint64_t)tile * a.per_cta + ti) * V;
+            W x[E][V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (row0 + v < a.nrows) {
+                    const W *gp = geo.row_ptr(a, row0 + v) + s0;
+                    if (B0 == 0) {
+#pragma unroll
+                        for (int q = 0; q < E / V; ++q) {
+                            W c[V];
+                            unpack(__ldcg(reinterpret_cast<const uint4 *>(gp) + q), c);
+#pragma unroll
+                            for (int k = 0; k < V; ++k) x[q * V + k][v] = c[k];
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < E; ++j) x[j][v] = __ldcg(gp + (j << B0));
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < E; ++j) x[j][v] = 0;
+                }
+            }
+            unit_round<W, DIR, VAR, LOGR, ROW, TVC, RI>(a, geo, tile, rp, ti, 0, s0, lo, x);
+        }
+        return;
+    }
     for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
         const uint32_t tv = u & ((1u << logTV) - 1u);
         const uint32_t g = (u >> logTV) & ((G::NS >> LE) - 1u);
@@ -599,8 +613,9 @@ __device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
     if (tile < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, tile, sm);
     cp_async_commit();
     for (uint32_t it = 0; tile < a.ntiles; tile += gridDim.x, ++it) {
-        uint4 *cur = (it & 1) ? sm + a.buf_chunks : sm;
-        uint4 *nxt = (it & 1) ? sm : sm + a.buf_chunks;
+        // row passes copy nothing ahead and use one buffer
+        uint4 *cur = (!ROW && (it & 1)) ? sm + a.buf_chunks : sm;
+        uint4 *nxt = (!ROW && (it & 1)) ? sm : sm + a.buf_chunks;
         const uint32_t next = tile + gridDim.x;
         if (next < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, next, nxt);
         cp_async_commit();

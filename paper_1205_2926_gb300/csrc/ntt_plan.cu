@@ -308,7 +308,7 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
         } else {
             s.ma = s.mb = nullptr;
         }
-        s.smem = (size_t)2 * s.buf_chunks * 16;  // double buffer
+        s.smem = (size_t)(kind == 1 ? 1 : 2) * s.buf_chunks * 16;  // column passes: double buffer
         cudaError_t e = launch(pl, s, kind, dir, st);
         if (e != cudaSuccess) return cuda_fail(e, "launch pass");
     }
