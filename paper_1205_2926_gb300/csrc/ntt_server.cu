@@ -75,6 +75,7 @@ struct ntt_server_s {
     size_t wbytes = 4;
     std::vector<cudaStream_t> streams;
     std::vector<double> stream_work;  // outstanding butterflies per stream
+    int next_stream = 0;              // where the next tie-break starts
     std::mutex mu;
     std::condition_variable cv, done_cv;
     std::deque<uint64_t> queue;
@@ -199,7 +200,18 @@ static void scheduler(ntt_server_s *sv) {
             bt.ids = kv.second;
             bt.bytes = 2 * kv.first * sv->wbytes * bt.ids.size();
             bt.work = (double)bfly_count(kv.first) * (double)bt.ids.size();
-            bt.stream = (int)(std::min_element(sv->stream_work.begin(), sv->stream_work.end()) - sv->stream_work.begin());
+            {
+                // least outstanding work; ties go round-robin so that small
+                // batches spread over the idle streams
+                const int ns = (int)sv->streams.size();
+                int best = sv->next_stream;
+                for (int k = 1; k < ns; ++k) {
+                    const int c = (sv->next_stream + k) % ns;
+                    if (sv->stream_work[c] < sv->stream_work[best]) best = c;
+                }
+                bt.stream = best;
+                sv->next_stream = (best + 1) % ns;
+            }
             cudaEventCreateWithFlags(&bt.done, cudaEventDisableTiming);
             std::vector<Request *> rs;
             for (uint64_t id : bt.ids) rs.push_back(&sv->reqs[id]);
