@@ -120,8 +120,6 @@ class ClockSampler:
 # workload and pass; passes without a capture report null.  The writes are 0:
 # the pass's output stays in the 129 MB L2 until it is evicted later.
 NCU_TRAFFIC = {
-    ("c2", "forward pass 0 of 64 x 2^16 (log2 R = 7)"): 17357568 + 0,
-    ("c2", "inverse pass 1 of 64 x 2^16 (log2 R = 7)"): 17368064 + 0,
 }
 
 

@@ -383,19 +383,28 @@ struct Geo {
     }
 };
 
-// Global -> shared copy of one CTA iteration of a column pass, issued as
-// cp.async copies (completed through commit/wait groups): consecutive threads
-// take consecutive 16-byte chunks of a tile row (coalesced), addresses advance
-// by constant strides from a per-thread base.  A row pass has nothing to copy
-// ahead: its first round gathers the V rows of each lane vector straight from
-// global memory (tile_round).
+// Which passes prefetch their tiles into shared memory with cp.async (double
+// buffered) and which let their first round load straight from global memory
+// into registers: the direct load is faster for every 32-bit pass and for
+// 64-bit row passes (measured); 64-bit column passes keep the prefetch.
+template <typename W, bool ROW>
+struct Prefetch {
+    static constexpr bool ON = !ROW && sizeof(W) == 8;
+};
+
+// Global -> shared copy of one CTA iteration of a prefetching column pass,
+// issued as cp.async copies (completed through commit/wait groups):
+// consecutive threads take consecutive 16-byte chunks of a tile row
+// (coalesced), addresses advance by constant strides from a per-thread base.
+// Other passes have nothing to copy ahead: their first round loads straight
+// from global memory (tile_round).
 template <typename W, int LOGR, bool ROW, int TVC>
 __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo, uint32_t tile,
                                           uint4 *buf) {
     using G = Geo<W, LOGR, ROW, TVC>;
     constexpr int V = Lanes<W>::V;
-    if (ROW) {
-        // row passes copy nothing ahead: their first round reads global memory
+    if (!Prefetch<W, ROW>::ON) {
+        // nothing to copy ahead: the first round reads global memory
     } else {
         const int logTV = geo.logTV();
         const uint32_t cc = threadIdx.x & ((1u << logTV) - 1u);
@@ -552,6 +561,37 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
         }
         return;
     }
+    if constexpr (!ROW && RI == 0 && !Prefetch<W, ROW>::ON) {
+        // First round of a column pass without prefetch: the unit's E vectors
+        // (rows s_j of its V adjacent columns, one 16-byte chunk each) come
+        // straight from global memory; the TV threads of a tile row read one
+        // contiguous 16*TV-byte run.  Loads go through L2 only.
+        for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
+            const uint32_t tv = u & ((1u << logTV) - 1u);
+            const uint32_t g = (u >> logTV) & ((G::NS >> LE) - 1u);
+            const uint32_t ti = u >> (logTV + G::LOGS - LE);
+            const uint32_t lo = g & ((1u << B0) - 1u);
+            const uint32_t s0 = ((g >> B0) << (B0 + LE)) | lo;
+            uint4 *rp = buf + ((ti * G::NSP + s0 + (s0 >> 3)) << logTV) + tv;
+            const uint32_t t = tile * a.per_cta + ti;
+            W x[E][V];
+            if (t < geo.sub_total) {
+                uint32_t ct;
+                const uint64_t S = 1ull << a.logS;
+                const W *gp = geo.col_origin(a, t, ct) + s0 * S + tv * V;
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    unpack(__ldcg(reinterpret_cast<const uint4 *>(gp + (uint64_t)(j << B0) * S)), x[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) x[j][v] = 0;
+            }
+            unit_round<W, DIR, VAR, LOGR, ROW, TVC, RI>(a, geo, tile, rp, ti, tv, s0, lo, x);
+        }
+        return;
+    }
     for (uint32_t u = threadIdx.x; u < units; u += kThreads) {
         const uint32_t tv = u & ((1u << logTV) - 1u);
         const uint32_t g = (u >> logTV) & ((G::NS >> LE) - 1u);
@@ -613,9 +653,10 @@ __device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
     if (tile < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, tile, sm);
     cp_async_commit();
     for (uint32_t it = 0; tile < a.ntiles; tile += gridDim.x, ++it) {
-        // row passes copy nothing ahead and use one buffer
-        uint4 *cur = (!ROW && (it & 1)) ? sm + a.buf_chunks : sm;
-        uint4 *nxt = (!ROW && (it & 1)) ? sm : sm + a.buf_chunks;
+        // passes without prefetch use one buffer
+        constexpr bool PF = Prefetch<W, ROW>::ON;
+        uint4 *cur = (PF && (it & 1)) ? sm + a.buf_chunks : sm;
+        uint4 *nxt = (PF && (it & 1)) ? sm : sm + a.buf_chunks;
         const uint32_t next = tile + gridDim.x;
         if (next < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, next, nxt);
         cp_async_commit();

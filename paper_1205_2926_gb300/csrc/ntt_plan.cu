@@ -308,7 +308,8 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
         } else {
             s.ma = s.mb = nullptr;
         }
-        s.smem = (size_t)(kind == 1 ? 1 : 2) * s.buf_chunks * 16;  // column passes: double buffer
+        // prefetching passes (64-bit column passes) double-buffer their tiles
+        s.smem = (size_t)(kind == 0 && pl->wbytes == 8 ? 2 : 1) * s.buf_chunks * 16;
         cudaError_t e = launch(pl, s, kind, dir, st);
         if (e != cudaSuccess) return cuda_fail(e, "launch pass");
     }
