@@ -75,6 +75,7 @@ struct ntt_server_s {
     size_t wbytes = 4;
     std::vector<cudaStream_t> streams;
     std::vector<double> stream_work;  // outstanding butterflies per stream
+    cudaMemPool_t pool = nullptr;     // the server's own stream-ordered pool
     int next_stream = 0;              // where the next tie-break starts
     std::mutex mu;
     std::condition_variable cv, done_cv;
@@ -108,7 +109,7 @@ static int launch_batch_t(ntt_server_s *sv, Batch &bt, const std::vector<Request
     ntt_plan_s *pl = bt.plan;
     const uint64_t L = pl->L, n = rs.size();
     const size_t wb = sizeof(W);
-    cudaError_t e = cudaMallocAsync(&bt.slab, bt.bytes, st);
+    cudaError_t e = cudaMallocFromPoolAsync(&bt.slab, bt.bytes, sv->pool, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "server slab");
     W *slab = (W *)bt.slab;
     e = cudaMemsetAsync(slab, 0, bt.bytes, st);
@@ -161,12 +162,19 @@ static void scheduler(ntt_server_s *sv) {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
     while (true) {
-        // 1. completions
+        // 1. completions (batches on one stream finish in order: once one
+        //    is still running, the later ones on its stream are not queried)
         bool progressed = false;
+        uint64_t busy = 0;  // streams with a batch still running (bit per stream)
         for (size_t i = 0; i < sv->inflight.size();) {
             Batch &bt = sv->inflight[i];
+            if (busy >> bt.stream & 1) {
+                ++i;
+                continue;
+            }
             cudaError_t q = cudaEventQuery(bt.done);
             if (q == cudaErrorNotReady) {
+                busy |= 1ull << bt.stream;
                 ++i;
                 continue;
             }
@@ -239,7 +247,8 @@ static void scheduler(ntt_server_s *sv) {
             sv->stream_work[bt.stream] += bt.work;
             sv->inflight.push_back(bt);
         }
-        // 4. wait for work: short sleeps while batches run, block when idle
+        // 4. wait for work: short sleeps while batches run (requests that
+        //    arrive meanwhile are admitted together), block when idle
         if (!sv->inflight.empty()) {
             lk.unlock();
             std::this_thread::sleep_for(std::chrono::microseconds(20));
@@ -288,6 +297,27 @@ int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out) {
         sv->streams.push_back(s);
     }
     sv->stream_work.assign(sv->streams.size(), 0.0);
+    {
+        // slabs come from a pool of the server's own that keeps up to the
+        // memory budget reserved between batches instead of returning it to
+        // the driver at every synchronisation (remapping costs milliseconds)
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = sv->device;
+        cudaError_t e = cudaMemPoolCreate(&sv->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = cfg->mem_budget_bytes;
+            e = cudaMemPoolSetAttribute(sv->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        if (e != cudaSuccess) {
+            if (sv->pool) cudaMemPoolDestroy(sv->pool);
+            for (cudaStream_t t : sv->streams) cudaStreamDestroy(t);
+            delete sv;
+            return cuda_fail(e, "server pool");
+        }
+    }
     sv->worker = std::thread(scheduler, sv);
     *out = sv;
     return NTT_OK;
@@ -432,6 +462,7 @@ int ntt_server_destroy(ntt_server_t sv) {
     }
     sv->worker.join();
     for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+    if (sv->pool) cudaMemPoolDestroy(sv->pool);
     delete sv;
     return NTT_OK;
 }
