@@ -120,6 +120,10 @@ class ClockSampler:
 # workload and pass; passes without a capture report null.  The writes are 0:
 # the pass's output stays in the 129 MB L2 until it is evicted later.
 NCU_TRAFFIC = {
+    ("c2", "forward pass 0 of 64 x 2^16 (log2 R = 7)"): 17356288 + 0,
+    ("c2", "forward pass 1 of 64 x 2^16 (log2 R = 9)"): 16805376 + 0,
+    ("c2", "inverse pass 0 of 64 x 2^16 (log2 R = 9)"): 16810496 + 0,
+    ("c2", "inverse pass 1 of 64 x 2^16 (log2 R = 7)"): 17366528 + 0,
 }
 
 

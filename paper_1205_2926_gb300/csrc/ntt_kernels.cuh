@@ -668,8 +668,16 @@ __device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
     cp_async_wait<0>();
 }
 
+// Resident CTAs per SM the register budget is cut for: 4 (64 registers) for
+// 32-bit passes up to R = 2^9, 3 (80 registers) for the longer 32-bit passes,
+// 2 for 64-bit words -- the faster choice per pass length (measured).
+template <typename W, int LOGR>
+struct Occupancy {
+    static constexpr int CTAS = sizeof(W) == 4 ? (LOGR <= 9 ? 4 : 3) : 2;
+};
+
 template <typename W, int DIR, int VAR, int LOGR, bool ROW>
-__global__ void __launch_bounds__(kThreads, sizeof(W) == 4 ? 3 : 2) k_pass(const PassArgs<W> a) {
+__global__ void __launch_bounds__(kThreads, (Occupancy<W, LOGR>::CTAS)) k_pass(const PassArgs<W> a) {
     extern __shared__ uint4 sm[];
     constexpr int TVF = ColWidth<LOGR>::LOGTV;
     if (ROW || a.logTV == TVF)
