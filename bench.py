@@ -24,6 +24,7 @@ import concurrent.futures
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -285,8 +286,9 @@ def time_steps(wl, torch, K, W, dist, graph=None, with_events=False):
     torch.cuda.synchronize()
     t1 = time.time()
     barrier(dist)
-    ms = sum(a.elapsed_time(b) for a, b in per_step)
-    return ms, events, (t0, t1)
+    steps_ms = [a.elapsed_time(b) for a, b in per_step]
+    wl.last_steps_ms = steps_ms
+    return sum(steps_ms), events, (t0, t1)
 
 
 def time_e2e(wl, torch, K, W, dist):
@@ -349,10 +351,24 @@ def cpu_sample(groups, budget_s):
     return done_bfly, t_used, "; ".join(parts)
 
 
+def host_cpu():
+    """The host CPU the oracle ran on: model name (lscpu) and logical cores."""
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "logical_cores": os.cpu_count()}
+
+
 def cpu_baseline_oracle(groups, budget_s=12.0):
     bf, t, desc = cpu_sample(groups, budget_s)
     return {"value": bf / t, "unit": "butterflies/s", "cores": 1, "kind": "oracle",
-            "sample": desc + f" of the same workload ({t:.1f} s, single thread)"}
+            "sample": desc + f" of the same workload ({t:.1f} s, single thread)", "host": host_cpu()}
 
 
 def run_uneven(args, dist, rank, world):
@@ -482,12 +498,19 @@ def run_serve_workload(args, dist, rank, world):
     t0 = time.time()
     res = run_serving(args.serve_seconds, 20000.0, torch, ntt)
     clocks = sampler.stop(t0, time.time())
+    # offered-load sweep around the configured rate (1 s each): where the
+    # latency knee lies
+    sweep = []
+    for rate in (10000.0, 40000.0, 80000.0, 160000.0):
+        r = run_serving(1.0, rate, torch, ntt, seed=6)
+        sweep.append({"offered_rate_per_s": rate, "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                      "throughput_req_per_s": r["throughput_req_per_s"], "refused": r["refused"]})
     return {
         "metric": METRIC, "value": res["p99_ms"], "unit": "ms (p99 polymul latency)", "n_gpus": world,
         "steps": res["requests"], "warmup": args.warmup, "ms_per_step": res["mean_ms"], "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded Poisson trace)",
         "config": {"workload": WORKLOADS["c5"]["name"], "seconds": args.serve_seconds},
-        "serving": res, "clocks": clocks,
+        "serving": res, "rate_sweep": sweep, "clocks": clocks,
     }
 
 
@@ -529,6 +552,7 @@ def run_ours(args, dist, rank, world):
     torch.cuda.synchronize()
     graph = capture_step(wl, torch)
     ms_lazy, _, (t0, t1) = time_steps(wl, torch, args.steps, args.warmup, dist, graph=graph)
+    lazy_steps = sorted(wl.last_steps_ms)
     clocks = sampler.stop(t0, t1)
     ms_lazy = max_over_ranks(ms_lazy, dist, torch)
     # per-kernel durations: the same step launched eagerly, CUDA events around each pass
@@ -582,6 +606,8 @@ def run_ours(args, dist, rank, world):
         "steps": K,
         "warmup": args.warmup,
         "ms_per_step": ms_lazy / K,
+        "step_ms": {"median": lazy_steps[len(lazy_steps) // 2],
+                    "p99": lazy_steps[min(len(lazy_steps) - 1, int(0.99 * len(lazy_steps)))]},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -636,7 +662,7 @@ def run_reference(args, rank, world):
         "data": "synthetic (seeded uniform residues)",
         "config": {"workload": spec["name"], "butterflies_per_step": bfly_step},
         "cpu_baseline": {"value": value, "unit": "butterflies/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: {desc} of the workload, single thread"},
+                         "sample": f"per step: {desc} of the workload, single thread", "host": host_cpu()},
         "e2e": {"value": value, "unit": "butterflies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -688,7 +714,8 @@ def run_reference_sampled(args, world):
         "warmup": args.warmup, "ms_per_step": None, "higher_is_better": hib, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
         "config": {"workload": WORKLOADS[args.workload]["name"]},
-        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     line.update(extra)
@@ -708,6 +735,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if "NTT_AUTOTUNE_CACHE" not in os.environ:
+        # start from the pass splits tuned on this GPU model (shipped with the
+        # package); a shape or GPU it lacks is tuned at run time into the copy
+        import shutil
+        import tempfile
+        cache = os.path.join(tempfile.mkdtemp(prefix="ntt_bench_"), "autotune.json")
+        shutil.copy(os.path.join(ROOT, "paper_1205_2926_gb300", "autotune_gb300.json"), cache)
+        os.environ["NTT_AUTOTUNE_CACHE"] = cache
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

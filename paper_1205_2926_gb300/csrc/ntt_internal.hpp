@@ -82,7 +82,9 @@ struct LaunchSpec {
 // Tile geometry of pass q of a plan for a batch (or, for a row pass over
 // single-row transforms, `rows` rows): fills logTV, per_cta, ntiles,
 // buf_chunks and nrows of the spec.
-void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s);
+// persistent: geometry for the uneven-batch kernel (column tiles of at most
+// 2048 vectors, its two buffers); otherwise for k_pass.
+void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s, bool persistent = false);
 cudaError_t launch_pass_u32(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
 cudaError_t launch_pass_u64(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
 

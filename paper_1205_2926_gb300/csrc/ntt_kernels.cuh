@@ -619,11 +619,22 @@ __device__ __forceinline__ void tile_rounds(const PassArgs<W> &a, const Geo<W, L
     }
 }
 
-// Widest column tile for a sub-transform length: R * TV <= 2048 vectors per
-// shared buffer, at most 8 vectors (128 bytes) per row.
-template <int LOGR>
+// Widest column tile for a sub-transform length: R * TV <= 2^LOGMAX vectors
+// per shared buffer, at most 8 vectors (128 bytes) per row.  Column passes of
+// R >= 2^10 that load their first round straight from global memory (one
+// buffer) take tiles of up to 4096 vectors (64 KiB), so that each tile row is
+// at least 64 bytes wide (measured: 20-30 % faster than 32- or 16-byte rows);
+// shorter ones stay at 2048 vectors, which keeps 4 CTAs per SM.  Prefetching
+// passes hold two buffers of up to 2048 vectors, and so does the uneven-batch
+// kernel.
+template <int LOGR, int LOGMAX = 11>
 struct ColWidth {
-    static constexpr int LOGTV = (11 - LOGR) < 3 ? (11 - LOGR) : 3;
+    static constexpr int LOGTV = (LOGMAX - LOGR) < 3 ? (LOGMAX - LOGR) : 3;
+};
+
+template <typename W, int LOGR>
+struct ColTileLog {
+    static constexpr int MAX = (!Prefetch<W, false>::ON && LOGR >= 10) ? 12 : 11;
 };
 
 // The two halves of one CTA iteration, for the persistent uneven-batch kernel
@@ -679,7 +690,7 @@ struct Occupancy {
 template <typename W, int DIR, int VAR, int LOGR, bool ROW>
 __global__ void __launch_bounds__(kThreads, (Occupancy<W, LOGR>::CTAS)) k_pass(const PassArgs<W> a) {
     extern __shared__ uint4 sm[];
-    constexpr int TVF = ColWidth<LOGR>::LOGTV;
+    constexpr int TVF = ColWidth<LOGR, ColTileLog<W, LOGR>::MAX>::LOGTV;
     if (ROW || a.logTV == TVF)
         pass_loop<W, DIR, VAR, LOGR, ROW, ROW ? 0 : TVF>(a, sm);
     else

@@ -316,7 +316,7 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
     return NTT_OK;
 }
 
-void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s) {
+void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s, bool persistent) {
     const PassPlan &ps = pl->pass[q];
     const int logV = pl->wbytes == 4 ? 2 : 1;
     const int logR = ps.logR;
@@ -330,7 +330,10 @@ void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s) {
         s.ntiles = (uint32_t)((s.nrows + rows_per_iter - 1) / rows_per_iter);
         s.buf_chunks = (uint32_t)s.per_cta * nsp;
     } else {  // column pass: R rows x TV vectors per sub-tile
-        int logTV = std::min(ps.logTV, std::max(0, 11 - logR));  // R * TV <= 2048 vectors per buffer
+        // R * TV <= 4096 vectors in the one buffer of a directly loading
+        // (32-bit) column pass with R >= 2^10, <= 2048 otherwise
+        const int logmax = (pl->wbytes == 4 && !persistent && logR >= 10) ? 12 : 11;
+        int logTV = std::min(ps.logTV, std::max(0, logmax - logR));
         while (logTV > 1 && (batch << (pl->logL - logR - logTV - logV)) < 4 * 152) --logTV;
         const uint32_t units = (1u << (logR + logTV)) >> 3;
         const uint32_t nsp = (1u << logR) + (1u << logR >> 3);

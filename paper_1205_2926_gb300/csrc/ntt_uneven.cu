@@ -298,7 +298,7 @@ static UStage make_stage(const ntt_plan_s *pl, int dir, int i, uint32_t nrows_cl
     memset(&s, 0, sizeof(s));
     s.nrows = nrows_class;
     // a large batch count: no tile narrowing (the batch itself fills the GPU)
-    tile_params(pl, q, 1u << 20, s);
+    tile_params(pl, q, 1u << 20, s, true);
     s.nrows = nrows_class ? nrows_class : (1ull << (pl->logL - ps.logR));
     s.ntiles = (uint32_t)((s.nrows + ((uint64_t)s.per_cta << 2) - 1) / ((uint64_t)s.per_cta << 2));
     if (q != n - 1) {
