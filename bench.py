@@ -50,6 +50,8 @@ WORKLOADS = {
     "c5": {"name": "polymul serving: Poisson 20k req/s, p = 998244353, degrees log-uniform 2^6..2^20",
            "groups": []},
     "probe": {"name": "register-only butterfly rate probe", "groups": []},
+    "bigint": {"name": "big-integer product: 2^22 x 2^22 limbs of 32 bits (3 NTT primes + CRT + carries)",
+               "groups": []},
 }
 
 
@@ -514,6 +516,54 @@ def run_serve_workload(args, dist, rank, world):
     }
 
 
+def run_bigint(args, dist, rank, world):
+    """Section 1's large-integer application: the product of two integers of
+    2^22 32-bit limbs (134 Mbit each) by three NTT polynomial products
+    (primes 998244353, 167772161, 469762049, L = 2^23), Chinese remaindering
+    and a carry scan (bigint_mul).  Timed with CUDA events, L2 flushed before
+    each product (parity of bigint_mul up to this size is in the tests)."""
+    import torch
+    import paper_1205_2926_gb300 as ntt
+    from paper_1205_2926_gb300 import build
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = 1 << 22
+    rng = np.random.default_rng(11)
+    a = torch.from_numpy(rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32).view(np.int32)).cuda()
+    b = torch.from_numpy(rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32).view(np.int32)).cuda()
+    c = torch.empty(2 * n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        ntt.bigint_mul(a, n, b, n, c)
+    torch.cuda.synchronize()
+    K = max(3, min(args.steps, 20))
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    t0 = time.time()
+    ms = []
+    for _ in range(K):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ntt.bigint_mul(a, n, b, n, c)
+        e1.record()
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    clocks = sampler.stop(t0, time.time())
+    times = sorted(x.elapsed_time(y) for x, y in ms)
+    mean = sum(times) / K
+    bfly = 3 * 3 * 23 * (1 << 22)  # three primes x (two forward + one inverse) transforms of 2^23
+    return {
+        "metric": "big-integer product time (2^22 x 2^22 32-bit limbs)", "value": mean, "unit": "ms per product",
+        "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": mean,
+        "step_ms": {"median": times[K // 2], "p99": times[-1]}, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded uniform limbs)",
+        "config": {"workload": WORKLOADS["bigint"]["name"], "l2": "flushed before each product (512 MiB write)"},
+        "input_mbit_per_s": 2 * 32 * n / (mean / 1e3) / 1e6, "transform_butterflies_per_s": bfly / (mean / 1e3),
+        "clocks": clocks,
+    }
+
+
 def run_probe():
     """Build and run csrc/probe/butterfly_rate.cu: register-only butterfly and
     multiply rates of this GPU (the integer-pipe roof of the NTT kernels)."""
@@ -565,6 +615,13 @@ def run_ours(args, dist, rank, world):
     graph_ntl = capture_step(wl, torch)
     ms_ntl, _, _ = time_steps(wl, torch, args.steps, args.warmup, dist, graph=graph_ntl)
     ms_ntl = max_over_ranks(ms_ntl, dist, torch)
+    # Algorithm 5 (Montgomery's product, lazy ranges) in the same schedule
+    wl.set_variant(2)
+    for _ in range(3):
+        wl.step()
+    graph_mont = capture_step(wl, torch)
+    ms_mont, _, _ = time_steps(wl, torch, args.steps, args.warmup, dist, graph=graph_mont)
+    ms_mont = max_over_ranks(ms_mont, dist, torch)
     wl.set_variant(0)
     k_e2e = max(3, min(args.steps, 50))
     ms_e2e = time_e2e(wl, torch, k_e2e, 2, dist)
@@ -619,6 +676,8 @@ def run_ours(args, dist, rank, world):
         "hbm_gbs_useful": world * bytes_step * K / (ms_lazy / 1e3) / 1e9,
         "ntl": {"value": ntl_value, "unit": "butterflies/s", "ms_per_step": ms_ntl / K},
         "lazy_over_ntl": ms_ntl / ms_lazy,
+        "montgomery": {"value": job_value(bfly_step * K, world, ms_mont / 1e3), "unit": "butterflies/s",
+                       "ms_per_step": ms_mont / K, "lazy_over_montgomery": ms_mont / ms_lazy},
         "roofline": roof,
         "kernels": {f"g{g}{'i' if i else 'f'}{s}": round(v["avg_ms"] * 1e3, 2) for (g, i, s), v in stats.items()},
         "e2e": {"value": world * bfly_step * k_e2e / (ms_e2e / 1e3), "unit": "butterflies/s",
@@ -749,6 +808,10 @@ def main():
     if args.impl == "reference" and args.workload == "probe":
         print(json.dumps({"impl": "reference", "unavailable": "the probe measures GPU pipes only"}))
         return
+    if args.impl == "reference" and args.workload == "bigint":
+        print(json.dumps({"impl": "reference", "unavailable": "an extra workload beyond the benchmark configurations; "
+                          "its oracle (exact CPU integer product) is used by the tests only"}))
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
         if line is not None:
@@ -765,6 +828,8 @@ def main():
         line = run_uneven(args, dist, rank, world)
     elif args.workload == "c5":
         line = run_serve_workload(args, dist, rank, world)
+    elif args.workload == "bigint":
+        line = run_bigint(args, dist, rank, world)
     else:
         line = run_ours(args, dist, rank, world)
     if rank == 0:

@@ -61,6 +61,8 @@ extern "C" {
 /* Butterfly variants (ntt_plan_set_variant). */
 #define NTT_VARIANT_LAZY 0 /* Algorithms 3 (forward) and 4 (inverse), redundant residues */
 #define NTT_VARIANT_NTL 1  /* Algorithm 2 and its fully reduced inverse (comparison baseline) */
+#define NTT_VARIANT_MONT 2 /* Algorithm 5 (Montgomery's product, lazy ranges) and its inverse
+                              counterpart (Algorithm 4 with Montgomery's product) */
 
 typedef struct ntt_plan_s *ntt_plan_t;
 
@@ -93,7 +95,12 @@ int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L);
 /* Free a plan and its device tables (synchronises the device first). */
 int ntt_plan_destroy(ntt_plan_t plan);
 
-/* Select NTT_VARIANT_LAZY or NTT_VARIANT_NTL for later calls on this plan. */
+/* Select NTT_VARIANT_LAZY, NTT_VARIANT_NTL or NTT_VARIANT_MONT for later calls
+ * on this plan.  The first selection of NTT_VARIANT_MONT builds the plan's
+ * tables in Montgomery form (W' = beta W mod p, Algorithm 5's input), kept
+ * beside the Shoup tables until the plan is destroyed or re-split; the
+ * variant's input and output ranges are those of NTT_VARIANT_LAZY.
+ * Errors: NTT_ERR_ARG, NTT_ERR_NOMEM. */
 int ntt_plan_set_variant(ntt_plan_t plan, int variant);
 
 /* Read-only description of a plan.  word_bytes is 4 or 8; n_passes is the
@@ -212,6 +219,24 @@ int polymul_mod_p(uint64_t p, const void *d_a, size_t na, const void *d_b, size_
  * too small), NTT_ERR_ALIGN, NTT_ERR_CUDA. */
 int polymul_mod_p_noalloc(ntt_plan_t plan, const void *d_a, size_t na, const void *d_b, size_t nb, void *d_c,
                           void *stream);
+
+/* ----------------------------------------------------- big-integer products */
+
+/* c = a * b for non-negative integers given as little-endian arrays of
+ * 32-bit limbs (device pointers; the application named in Section 1:
+ * integers multiplied as polynomials evaluated at 2^32).  The coefficients of
+ * the polynomial product are below min(na, nb) (2^32 - 1)^2 < 2^86; they are
+ * computed by three polynomial products modulo 998244353, 167772161 and
+ * 469762049 (forward transforms with Algorithm 3, pointwise product,
+ * inverse transform with Algorithm 4), combined by Chinese remaindering
+ * (Garner's form), and their words summed with a parallel carry scan.
+ * c receives na + nb limbs (the top one may be 0); a and b are not modified
+ * and may not overlap c.  Limits: na + nb - 1 <= 2^23.  Device scratch of
+ * 24 (nextpow2(na + nb - 1)) bytes comes from cudaMallocAsync on `stream`.
+ * Asynchronous on `stream`.
+ * Errors: NTT_ERR_ARG (null pointer or zero length), NTT_ERR_RANGE, NTT_ERR_NOMEM,
+ * NTT_ERR_CUDA. */
+int bigint_mul(const uint32_t *d_a, size_t na, const uint32_t *d_b, size_t nb, uint32_t *d_c, void *stream);
 
 /* ------------------------------------------------------------- uneven batch */
 

@@ -18,6 +18,9 @@ Functions and the passages they follow (Harvey, arXiv:1205.2926):
   application of Section 1 (definition, and the convolution theorem).
 * ``is_prime``, ``smallest_qnr``, ``find_prime_above``, ``root_of_unity`` --
   number theory that names the primes p = 1 mod L and the roots omega.
+* ``bigint_mul`` -- the large-integer application of Section 1: the product
+  of two integers given as little-endian 32-bit limbs, by Python's exact
+  integer arithmetic (the definition; no transform involved).
 """
 from __future__ import annotations
 
@@ -215,3 +218,21 @@ def polymul_ntt(p, a, b):
 
 def root_of_unity(p, L):
     return get().root_of_unity(p, L)
+
+
+def limbs_to_int(limbs) -> int:
+    """Little-endian 32-bit limbs -> Python integer."""
+    return int.from_bytes(np.asarray(limbs, dtype="<u4").tobytes(), "little")
+
+
+def int_to_limbs(v: int, n: int) -> np.ndarray:
+    """Python integer (0 <= v < 2^(32 n)) -> n little-endian 32-bit limbs."""
+    return np.frombuffer(v.to_bytes(4 * n, "little"), dtype="<u4").astype(np.uint32)
+
+
+def bigint_mul(a, b) -> np.ndarray:
+    """Product of two integers given as little-endian 32-bit limb arrays, as
+    len(a) + len(b) limbs (Section 1's large-integer application, computed
+    from the definition with exact integers)."""
+    na, nb = len(a), len(b)
+    return int_to_limbs(limbs_to_int(a) * limbs_to_int(b), na + nb)

@@ -19,6 +19,7 @@ from ._lib import NTTError, check
 
 VARIANT_LAZY = 0
 VARIANT_NTL = 1
+VARIANT_MONT = 2
 
 
 def _ptr(x) -> int:
@@ -144,6 +145,12 @@ def ntt_transform_host(plan: Plan, inverse: bool, host_array, batch: int, stride
 
 def polymul_mod_p(p: int, a, na: int, b, nb: int, c, stream=None) -> None:
     check(_lib.load().polymul_mod_p(p, _ptr(a), na, _ptr(b), nb, _ptr(c), _stream(stream)), "polymul_mod_p")
+
+
+def bigint_mul(a, na: int, b, nb: int, c, stream=None) -> None:
+    """c = a * b for integers as little-endian 32-bit limb arrays on the device
+    (c has na + nb limbs); see the C header for the limits."""
+    check(_lib.load().bigint_mul(_ptr(a), na, _ptr(b), nb, _ptr(c), _stream(stream)), "bigint_mul")
 
 
 def polymul_mod_p_noalloc(plan: Plan, a, na: int, b, nb: int, c, stream=None) -> None:

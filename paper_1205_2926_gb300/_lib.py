@@ -65,6 +65,7 @@ _SIGNATURES = {
     "ntt_execute_step": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size, c_size, c_void_p]),
     "ntt_transform_host": (c_int, [c_void_p, c_int, c_void_p, c_size, c_size, c_void_p]),
     "polymul_mod_p": (c_int, [c_u64, c_void_p, c_size, c_void_p, c_size, c_void_p, c_void_p]),
+    "bigint_mul": (c_int, [c_void_p, c_size, c_void_p, c_size, c_void_p, c_void_p]),
     "polymul_mod_p_noalloc": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_size, c_void_p, c_void_p]),
     "ntt_execute_uneven": (c_int, [ctypes.POINTER(Desc), c_size, c_void_p]),
     "ntt_uneven_status": (c_int, [ctypes.POINTER(c_int)]),

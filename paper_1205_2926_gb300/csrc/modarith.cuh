@@ -196,6 +196,19 @@ NTT_HD void bfly_fwd_mont(W &x, W &y, W wm, W J, W p, W p2) {
     x = s;
 }
 
+// Inverse counterpart of Algorithm 5 (the paper gives the forward butterfly
+// only; this is Algorithm 4 with Montgomery's product in place of Shoup's):
+// X, Y in [0, 4p); X reduced once by 2p; T = W Y mod p in [0, 2p) by
+// mont_mul (valid for Y < 4p when p < beta/4: R1 < p); X' = X + T,
+// Y' = X - T + 2p, both in [0, 4p).
+template <typename W>
+NTT_HD void bfly_inv_mont(W &x, W &y, W wm, W J, W p, W p2) {
+    W a = csub(x, p2);
+    W t = mont_mul(y, wm, J, p);
+    x = (W)(a + t);
+    y = (W)(a - t + p2);
+}
+
 // Final normalisation (end of Section 3): [0, 2p) -> [0, p), [0, 4p) -> [0, p).
 template <typename W>
 NTT_HD W reduce2(W x, W p) {

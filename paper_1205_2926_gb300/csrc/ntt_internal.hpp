@@ -34,6 +34,8 @@ struct PassPlan {
     bool has_mb = false;
     void *ma[2] = {nullptr, nullptr};  // [direction] middle tables
     void *mb[2] = {nullptr, nullptr};
+    void *mam[2] = {nullptr, nullptr};  // the same in Montgomery form (second word beta W mod p)
+    void *mbm[2] = {nullptr, nullptr};
 };
 
 }  // namespace ntt
@@ -47,6 +49,9 @@ struct ntt_plan_s {
     int npass = 0;
     ntt::PassPlan pass[ntt::kMaxPasses];
     void *tw[2] = {nullptr, nullptr};  // stage tables per direction
+    void *twm[2] = {nullptr, nullptr}; // the same in Montgomery form (built on first use)
+    bool mont = false;                 // Montgomery tables present
+    uint64_t J = 0;                    // p^-1 mod beta
     int tw_log = 0;                    // tables cover distances m < 2^tw_log
     uint64_t table_bytes = 0;
     // host-buffer staging (ntt_transform_host): a device copy of the batch,
@@ -74,6 +79,7 @@ struct LaunchSpec {
     uint32_t flags;
     const void *tw, *ma, *mb;
     uint64_t p;
+    uint64_t J;           // p^-1 mod beta (Montgomery variant)
     uint64_t nrows;
     unsigned grid;  // tiny kernel only
     size_t smem;    // dynamic shared memory of the launch

@@ -56,7 +56,11 @@
 namespace ntt {
 
 enum { DIR_FWD = 0, DIR_INV = 1 };
-enum { VAR_LAZY = 0, VAR_NTL = 1 };
+// Butterfly variants: Algorithms 3-4 (lazy, Shoup's product), Algorithm 2 and
+// its fully reduced inverse (NTL-style), and Algorithm 5 with its inverse
+// counterpart (lazy ranges, Montgomery's product; the twiddle pairs then hold
+// (W, beta W mod p)).
+enum { VAR_LAZY = 0, VAR_NTL = 1, VAR_MONT = 2 };
 enum { F_NORMALIZE = 1, F_MIDDLE = 2, F_MB = 4 };
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels
@@ -85,6 +89,7 @@ struct PassArgs {
     const W *ma;          // middle twiddle pairs MA[s][c mod TA]
     const W *mb;          // middle twiddle pairs MB[c / TA][s]
     W p;
+    W J;                  // p^-1 mod beta (Montgomery variant)
     uint64_t nrows;       // row pass: number of rows (batch * L / R, or transforms)
     W *const *rowptrs;    // row pass over single-row transforms: address of each row (else null)
 };
@@ -161,15 +166,19 @@ __device__ __forceinline__ uint4 pack(const W (&x)[Lanes<W>::V]) {
 }
 
 template <typename W, int DIR, int VAR>
-__device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2) {
+__device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2, W J) {
     if (DIR == DIR_FWD) {
         if (VAR == VAR_LAZY)
             bfly_fwd_lazy(x, y, w, wq, p, p2);
+        else if (VAR == VAR_MONT)
+            bfly_fwd_mont(x, y, wq, J, p, p2);
         else
             bfly_fwd_ntl(x, y, w, wq, p);
     } else {
         if (VAR == VAR_LAZY)
             bfly_inv_lazy(x, y, w, wq, p, p2);
+        else if (VAR == VAR_MONT)
+            bfly_inv_mont(x, y, wq, J, p, p2);
         else
             bfly_inv_ntl(x, y, w, wq, p);
     }
@@ -179,12 +188,12 @@ __device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2) {
 template <typename W, int DIR, int VAR>
 __device__ __forceinline__ void bfly_w1(W &x, W &y, W p, W p2) {
     if (DIR == DIR_FWD) {
-        if (VAR == VAR_LAZY)
+        if (VAR != VAR_NTL)
             bfly_fwd_lazy_w1(x, y, p2);
         else
             bfly_fwd_ntl_w1(x, y, p);
     } else {
-        if (VAR == VAR_LAZY)
+        if (VAR != VAR_NTL)
             bfly_inv_lazy_w1(x, y, p2);
         else
             bfly_inv_ntl_w1(x, y, p);
@@ -192,8 +201,9 @@ __device__ __forceinline__ void bfly_w1(W &x, W &y, W p, W p2) {
 }
 
 template <typename W, int VAR>
-__device__ __forceinline__ W mul_twiddle(W x, W w, W wq, W p) {
-    W y = shoup_mul(x, w, wq, p);  // any x < beta -> [0, 2p)
+__device__ __forceinline__ W mul_twiddle(W x, W w, W wq, W p, W J) {
+    if (VAR == VAR_MONT) return mont_mul(x, wq, J, p);  // x < 4p -> [0, 2p)
+    W y = shoup_mul(x, w, wq, p);                       // any x < beta -> [0, 2p)
     return VAR == VAR_NTL ? csub(y, p) : y;
 }
 
@@ -224,7 +234,8 @@ struct Sched {
 // SKIP1 leaves out the stage of distance 1 (lb = 0 in the round with
 // b0 = 0), which the caller fuses with the middle twiddle.
 template <typename W, int DIR, int VAR, int LE, int B0, int NST, bool SKIP1 = false>
-__device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W *__restrict__ twp, W p, W p2) {
+__device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W *__restrict__ twp, W p, W p2,
+                                           W J) {
     constexpr int V = Lanes<W>::V;
     constexpr int E = 1 << LE;
 #pragma unroll
@@ -247,7 +258,7 @@ __device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W
                 for (int jh = 0; jh < E; jh += (2 << lb)) {
 #pragma unroll
                     for (int v = 0; v < V; ++v)
-                        bfly<W, DIR, VAR>(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w, wq, p, p2);
+                        bfly<W, DIR, VAR>(x[jh + jl][v], x[jh + jl + (1 << lb)][v], w, wq, p, p2, J);
                 }
             }
         }
@@ -256,7 +267,7 @@ __device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W
 
 template <typename W, int DIR, int VAR, int E>
 __device__ __forceinline__ void normalize(W (&x)[E][Lanes<W>::V], W p, W p2) {
-    if constexpr (VAR == VAR_LAZY) {
+    if constexpr (VAR != VAR_NTL) {
 #pragma unroll
         for (int j = 0; j < E; ++j)
 #pragma unroll
@@ -282,19 +293,20 @@ __device__ __forceinline__ void middle_twiddle(W (&x)[E][Lanes<W>::V], uint32_t 
             W w, wq;
             ld_pair(mbp, j, w, wq);
 #pragma unroll
-            for (int v = 0; v < V; ++v) x[j][v] = mul_twiddle<W, VAR>(x[j][v], w, wq, a.p);
+            for (int v = 0; v < V; ++v) x[j][v] = mul_twiddle<W, VAR>(x[j][v], w, wq, a.p, a.J);
         }
         W w[V], wq[V];
         ld_pairs<W>(map, j << a.logTA, w, wq);
 #pragma unroll
-        for (int v = 0; v < V; ++v) x[j][v] = mul_twiddle<W, VAR>(x[j][v], w[v], wq[v], a.p);
+        for (int v = 0; v < V; ++v) x[j][v] = mul_twiddle<W, VAR>(x[j][v], w[v], wq[v], a.p, a.J);
     }
 }
 
 // Distance-1 stage (W = 1) fused with the middle twiddle of a forward column
 // pass: X' = M_s (X + Y), Y' = M_{s+1} (X - Y + 2p).  Shoup's product accepts
-// any input below beta, so the two reductions of the W = 1 butterfly go away
-// (lazy variant; the NTL variant keeps its reductions).
+// any input below beta and Montgomery's any below 4p, so the two reductions
+// of the W = 1 butterfly go away (lazy variants; the NTL variant keeps its
+// reductions).
 template <typename W, int VAR, int E>
 __device__ __forceinline__ void last_stage_and_twiddle(W (&x)[E][Lanes<W>::V], uint32_t s0, uint32_t c0, uint32_t R,
                                                        const PassArgs<W> &a) {
@@ -304,7 +316,7 @@ __device__ __forceinline__ void last_stage_and_twiddle(W (&x)[E][Lanes<W>::V], u
     for (int j = 0; j < E; j += 2) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            if (VAR == VAR_LAZY) {
+            if (VAR != VAR_NTL) {
                 const W s = (W)(x[j][v] + x[j + 1][v]);
                 const W t = (W)(x[j][v] - x[j + 1][v] + p2);
                 x[j][v] = s;
@@ -330,7 +342,7 @@ __device__ __forceinline__ void twiddle_and_first_stage(W (&x)[E][Lanes<W>::V], 
     for (int j = 0; j < E; j += 2) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            if (VAR == VAR_LAZY) {
+            if (VAR != VAR_NTL) {
                 const W s = (W)(x[j][v] + x[j + 1][v]);
                 const W t = (W)(x[j][v] - x[j + 1][v] + p2);
                 x[j][v] = s;
@@ -456,11 +468,11 @@ __device__ __forceinline__ void unit_round(const PassArgs<W> &a, const Geo<W, LO
     constexpr bool FUSE = !ROW && B0 == 0 && LE == 3 && ((DIR == DIR_INV && FIRST) || (DIR == DIR_FWD && LAST));
     if (FUSE && mid) {
         if (DIR == DIR_INV) twiddle_and_first_stage<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
-        round_regs<W, DIR, VAR, LE, B0, NST, true>(x, a.tw + 2 * lo, p, p2);
+        round_regs<W, DIR, VAR, LE, B0, NST, true>(x, a.tw + 2 * lo, p, p2, a.J);
         if (DIR == DIR_FWD) last_stage_and_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
     } else {
         if (DIR == DIR_INV && FIRST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
-        round_regs<W, DIR, VAR, LE, B0, NST>(x, a.tw + 2 * lo, p, p2);
+        round_regs<W, DIR, VAR, LE, B0, NST>(x, a.tw + 2 * lo, p, p2, a.J);
         if (DIR == DIR_FWD && LAST && mid) middle_twiddle<W, VAR, E>(x, s0, c0, 1u << LOGR, a);
     }
     if (LAST && (a.flags & F_NORMALIZE)) normalize<W, DIR, VAR, E>(x, p, p2);
@@ -715,7 +727,7 @@ __global__ void k_tiny(const PassArgs<W> a) {
                 for (int k = 0; k < m; ++k) {
                     W w, wq;
                     ld_pair(a.tw, m + k, w, wq);
-                    bfly<W, DIR, VAR>(x[t + k], x[t + k + m], w, wq, p, p2);
+                    bfly<W, DIR, VAR>(x[t + k], x[t + k + m], w, wq, p, p2, a.J);
                 }
     } else {
         for (int m = 1; m < L; m <<= 1)
@@ -723,12 +735,12 @@ __global__ void k_tiny(const PassArgs<W> a) {
                 for (int k = 0; k < m; ++k) {
                     W w, wq;
                     ld_pair(a.tw, m + k, w, wq);
-                    bfly<W, DIR, VAR>(x[t + k], x[t + k + m], w, wq, p, p2);
+                    bfly<W, DIR, VAR>(x[t + k], x[t + k + m], w, wq, p, p2, a.J);
                 }
     }
     for (int i = 0; i < L; ++i) {
         W v = x[i];
-        if (VAR == VAR_LAZY) v = DIR == DIR_FWD ? reduce2(v, p) : reduce4(v, p, p2);
+        if (VAR != VAR_NTL) v = DIR == DIR_FWD ? reduce2(v, p) : reduce4(v, p, p2);
         d[i] = v;
     }
 }

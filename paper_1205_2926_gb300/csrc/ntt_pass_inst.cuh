@@ -28,6 +28,7 @@ static PassArgs<W> to_args(const LaunchSpec &s) {
     a.ma = static_cast<const W *>(s.ma);
     a.mb = static_cast<const W *>(s.mb);
     a.p = (W)s.p;
+    a.J = (W)s.J;
     a.nrows = s.nrows;
     a.rowptrs = nullptr;
     return a;
@@ -99,10 +100,8 @@ static cudaError_t launch_kind(const LaunchSpec &s, int kind, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Launch for one direction (instantiated in its own translation unit).
-template <typename W, int DIR>
-static cudaError_t launch_pass_dir(const LaunchSpec &s, int kind, int var, cudaStream_t st) {
-    return var == VAR_LAZY ? launch_kind<W, DIR, VAR_LAZY>(s, kind, st) : launch_kind<W, DIR, VAR_NTL>(s, kind, st);
-}
+// One (word type, direction, variant) per translation unit
+// (ntt_pass_<word>_<dir>_<variant>.cu), so that the instantiations compile in
+// parallel; ntt_pass_u32.cu / ntt_pass_u64.cu dispatch to them.
 
 }  // namespace ntt

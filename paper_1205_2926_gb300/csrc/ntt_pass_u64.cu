@@ -1,11 +1,19 @@
-// Dispatch of the pass kernels for 64-bit words to the per-direction units.
+// Dispatch of the pass kernels for 64-bit words to the per-(direction, variant) units.
 #include "ntt_internal.hpp"
 
 namespace ntt {
-cudaError_t launch_pass_u64_fwd(const LaunchSpec &s, int kind, int var, cudaStream_t st);
-cudaError_t launch_pass_u64_inv(const LaunchSpec &s, int kind, int var, cudaStream_t st);
+cudaError_t launch_pass_u64_fwd_lazy(const LaunchSpec &s, int kind, cudaStream_t st);
+cudaError_t launch_pass_u64_fwd_ntl(const LaunchSpec &s, int kind, cudaStream_t st);
+cudaError_t launch_pass_u64_fwd_mont(const LaunchSpec &s, int kind, cudaStream_t st);
+cudaError_t launch_pass_u64_inv_lazy(const LaunchSpec &s, int kind, cudaStream_t st);
+cudaError_t launch_pass_u64_inv_ntl(const LaunchSpec &s, int kind, cudaStream_t st);
+cudaError_t launch_pass_u64_inv_mont(const LaunchSpec &s, int kind, cudaStream_t st);
 
 cudaError_t launch_pass_u64(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st) {
-    return dir == 0 ? launch_pass_u64_fwd(s, kind, var, st) : launch_pass_u64_inv(s, kind, var, st);
+    if (dir == 0)
+        return var == 0 ? launch_pass_u64_fwd_lazy(s, kind, st)
+                        : var == 1 ? launch_pass_u64_fwd_ntl(s, kind, st) : launch_pass_u64_fwd_mont(s, kind, st);
+    return var == 0 ? launch_pass_u64_inv_lazy(s, kind, st)
+                    : var == 1 ? launch_pass_u64_inv_ntl(s, kind, st) : launch_pass_u64_inv_mont(s, kind, st);
 }
 }  // namespace ntt

@@ -133,14 +133,17 @@ static int max_logtv(int logS, int wbytes) {
 
 static void free_tables(ntt_plan_s *pl) {
     for (int d = 0; d < 2; ++d) {
-        if (pl->tw[d]) cudaFree(pl->tw[d]);
-        pl->tw[d] = nullptr;
-        for (int q = 0; q < kMaxPasses; ++q) {
-            if (pl->pass[q].ma[d]) cudaFree(pl->pass[q].ma[d]);
-            if (pl->pass[q].mb[d]) cudaFree(pl->pass[q].mb[d]);
-            pl->pass[q].ma[d] = pl->pass[q].mb[d] = nullptr;
+        for (void **t : {&pl->tw[d], &pl->twm[d]}) {
+            if (*t) cudaFree(*t);
+            *t = nullptr;
         }
+        for (int q = 0; q < kMaxPasses; ++q)
+            for (void **t : {&pl->pass[q].ma[d], &pl->pass[q].mb[d], &pl->pass[q].mam[d], &pl->pass[q].mbm[d]}) {
+                if (*t) cudaFree(*t);
+                *t = nullptr;
+            }
     }
+    pl->mont = false;
     pl->table_bytes = 0;
 }
 
@@ -167,17 +170,23 @@ static int upload_pairs(ntt_plan_s *pl, const std::vector<uint64_t> &pairs, void
     return NTT_OK;
 }
 
-static inline void push_pair(std::vector<uint64_t> &v, uint64_t w, uint64_t p, int bits) {
-    v.push_back(w);
-    v.push_back(nt::shoup_quotient(w, p, bits));
+// Second word of a twiddle pair: Shoup's quotient floor(W beta / p)
+// (Algorithms 2-4) or the Montgomery form beta W mod p (Algorithm 5).
+static inline uint64_t second_word(uint64_t w, uint64_t p, int bits, bool mont) {
+    if (!mont) return nt::shoup_quotient(w, p, bits);
+    return (uint64_t)(((unsigned __int128)w << bits) % p);
 }
 
-// Build every device table of the plan for its current split.
-static int build_tables(ntt_plan_s *pl) {
-    free_tables(pl);
+static inline void push_pair(std::vector<uint64_t> &v, uint64_t w, uint64_t p, int bits, bool mont) {
+    v.push_back(w);
+    v.push_back(second_word(w, p, bits, mont));
+}
+
+// Build the device tables of the plan for its current split, in Shoup form
+// (tw, ma, mb) or in Montgomery form (twm, mam, mbm).
+static int build_tables_form(ntt_plan_s *pl, bool mont) {
     const uint64_t p = pl->p;
     const int bits = pl->wbytes * 8;
-    const int logV = pl->wbytes == 4 ? 2 : 1;
     int maxr = 0;
     for (int q = 0; q < pl->npass; ++q) maxr = std::max(maxr, pl->pass[q].logR);
     pl->tw_log = std::max(2, maxr);  // lane stages read entries 1..3
@@ -187,18 +196,18 @@ static int build_tables(ntt_plan_s *pl) {
         // entry 0 is unused (set to W = 1)
         std::vector<uint64_t> tw;
         tw.reserve(2 * ((size_t)1 << pl->tw_log));
-        push_pair(tw, 1, p, bits);
+        push_pair(tw, 1, p, bits, mont);
         for (int b = 0; b < pl->tw_log; ++b) {
             const uint64_t m = 1ull << b;
             const uint64_t step = nt::powmod(root, pl->L / (2 * m), p);
             uint64_t w = 1;
             for (uint64_t k = 0; k < m; ++k) {
-                push_pair(tw, w, p, bits);
+                push_pair(tw, w, p, bits, mont);
                 w = nt::mulmod(w, step, p);
             }
         }
         tw.resize(2 * ((size_t)1 << pl->tw_log));  // 2^tw_log entries: [0] + m in [1, 2^tw_log)
-        int rc = upload_pairs(pl, tw, &pl->tw[d]);
+        int rc = upload_pairs(pl, tw, mont ? &pl->twm[d] : &pl->tw[d]);
         if (rc) return rc;
         // middle tables of the column passes
         int logB = pl->logL;
@@ -213,11 +222,11 @@ static int build_tables(ntt_plan_s *pl) {
                 const uint64_t z = nt::powmod(root, (u * nt::bitrev((uint32_t)s, logR)) % pl->L, p);
                 uint64_t w = 1;
                 for (uint64_t c = 0; c < (1ull << ps.logTA); ++c) {
-                    push_pair(ma, w, p, bits);
+                    push_pair(ma, w, p, bits, mont);
                     w = nt::mulmod(w, z, p);
                 }
             }
-            rc = upload_pairs(pl, ma, &ps.ma[d]);
+            rc = upload_pairs(pl, ma, mont ? &ps.mam[d] : &ps.ma[d]);
             if (rc) return rc;
             if (ps.has_mb) {
                 const uint64_t nhi = 1ull << (logS - ps.logTA);
@@ -227,18 +236,26 @@ static int build_tables(ntt_plan_s *pl) {
                     uint64_t w = 1;
                     for (uint64_t chi = 0; chi < nhi; ++chi) {
                         mb[2 * (chi * R + s)] = w;
-                        mb[2 * (chi * R + s) + 1] = nt::shoup_quotient(w, p, bits);
+                        mb[2 * (chi * R + s) + 1] = second_word(w, p, bits, mont);
                         w = nt::mulmod(w, zt, p);
                     }
                 }
-                rc = upload_pairs(pl, mb, &ps.mb[d]);
+                rc = upload_pairs(pl, mb, mont ? &ps.mbm[d] : &ps.mb[d]);
                 if (rc) return rc;
             }
             logB -= logR;
         }
     }
-    (void)logV;
+    if (mont) pl->mont = true;
     return NTT_OK;
+}
+
+static int build_tables(ntt_plan_s *pl) {
+    const bool mont = pl->mont;
+    free_tables(pl);
+    int rc = build_tables_form(pl, false);
+    if (rc == NTT_OK && (mont || pl->variant == NTT_VARIANT_MONT)) rc = build_tables_form(pl, true);
+    return rc;
 }
 
 static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
@@ -267,8 +284,11 @@ static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
 
 // ---------------------------------------------------------------- launches
 
+static_assert(NTT_VARIANT_LAZY == VAR_LAZY && NTT_VARIANT_NTL == VAR_NTL && NTT_VARIANT_MONT == VAR_MONT,
+              "the C-ABI variant numbers select the kernel variants directly");
+
 static cudaError_t launch(const ntt_plan_s *pl, const LaunchSpec &s, int kind, int dir, cudaStream_t st) {
-    const int var = pl->variant == NTT_VARIANT_NTL ? 1 : 0;
+    const int var = pl->variant;  // NTT_VARIANT_LAZY, _NTL or _MONT: 0, 1, 2
     return pl->wbytes == 4 ? launch_pass_u32(s, kind, dir, var, st) : launch_pass_u64(s, kind, dir, var, st);
 }
 
@@ -285,7 +305,9 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
     s.batch = (uint32_t)batch;
     s.logL = pl->logL;
     s.p = pl->p;
-    s.tw = pl->tw[dir];
+    s.J = pl->J;
+    const bool mont = pl->variant == NTT_VARIANT_MONT;
+    s.tw = mont ? pl->twm[dir] : pl->tw[dir];
     if (pl->logL <= 2) {
         s.grid = (unsigned)((batch + 127) / 128);
         cudaError_t e = launch(pl, s, 2, dir, st);
@@ -303,8 +325,8 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
         if (kind == 0) {
             s.logTA = ps.logTA;
             s.flags |= 2 | (ps.has_mb ? 4 : 0);  // F_MIDDLE, F_MB
-            s.ma = ps.ma[dir];
-            s.mb = ps.mb[dir];
+            s.ma = mont ? ps.mam[dir] : ps.ma[dir];
+            s.mb = mont ? ps.mbm[dir] : ps.mb[dir];
         } else {
             s.ma = s.mb = nullptr;
         }
@@ -424,6 +446,11 @@ int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L) {
     pl->L_inv = nt::powmod(L % p, p - 2, p);
     pl->logL = ilog2u(L);
     pl->wbytes = p < (1ull << 30) ? 4 : 8;
+    {
+        uint64_t inv = 1;  // p^-1 mod 2^64 by Newton's iteration (p odd); its low word is p^-1 mod 2^32
+        for (int i = 0; i < 6; ++i) inv *= 2 - p * inv;
+        pl->J = pl->wbytes == 4 ? (inv & 0xffffffffu) : inv;
+    }
     cudaGetDevice(&pl->device);
     int logr[kMaxPasses];
     int n = default_split(pl->logL, pl->wbytes, logr);
@@ -447,7 +474,13 @@ int ntt_plan_destroy(ntt_plan_t pl) {
 }
 
 int ntt_plan_set_variant(ntt_plan_t pl, int variant) {
-    if (!pl || (variant != NTT_VARIANT_LAZY && variant != NTT_VARIANT_NTL)) return NTT_ERR_ARG;
+    if (!pl || (variant != NTT_VARIANT_LAZY && variant != NTT_VARIANT_NTL && variant != NTT_VARIANT_MONT))
+        return NTT_ERR_ARG;
+    if (variant == NTT_VARIANT_MONT && !pl->mont) {
+        std::lock_guard<std::mutex> lk(pl->mu);
+        int rc = build_tables_form(pl, true);
+        if (rc) return rc;
+    }
     pl->variant = variant;
     return NTT_OK;
 }

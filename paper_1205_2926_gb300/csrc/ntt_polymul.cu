@@ -87,6 +87,23 @@ int polymul_validate(uint64_t p, size_t na, size_t nb, uint64_t *L_out) {
 }
 
 template <typename W>
+static int enqueue_pointwise_t(ntt_plan_s *pl, W *A, const W *B, uint64_t L, cudaStream_t st) {
+    const int bits = pl->wbytes * 8;
+    uint64_t J = 1;
+    for (int i = 0; i < 7; ++i) J *= 2 - pl->p * J;
+    const uint64_t K = (uint64_t)(((unsigned __int128)pl->L_inv << bits) % pl->p);
+    const uint64_t Kq = nt::shoup_quotient(K, pl->p, bits);
+    k_pointwise<W><<<grid_for(L), 256, 0, st>>>(A, B, L, (W)pl->p, (W)J, (W)K, (W)Kq);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "k_pointwise");
+}
+
+int enqueue_pointwise(ntt_plan_s *pl, void *A, const void *B, uint64_t L, cudaStream_t st) {
+    if (pl->wbytes == 4) return enqueue_pointwise_t<uint32_t>(pl, (uint32_t *)A, (const uint32_t *)B, L, st);
+    return enqueue_pointwise_t<uint64_t>(pl, (uint64_t *)A, (const uint64_t *)B, L, st);
+}
+
+template <typename W>
 static int enqueue_polymul_t(ntt_plan_s *pl, const W *a, size_t na, const W *b, size_t nb, W *c, W *buf,
                              cudaStream_t st) {
     const uint64_t L = pl->L, n = (uint64_t)na + nb - 1;

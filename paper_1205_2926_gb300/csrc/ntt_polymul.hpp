@@ -16,6 +16,10 @@ int polymul_validate(uint64_t p, size_t na, size_t nb, uint64_t *L_out);
 // Cached plan for (current device, p, L) with the library's root of unity.
 int polymul_plan(uint64_t p, uint64_t L, ntt_plan_s **out);
 
+// Enqueue A <- A B L^-1 mod p over L words (transforms in [0, 2p) from the
+// forward pass; result in [0, 2p), the inverse pass's input range).
+int enqueue_pointwise(ntt_plan_s *pl, void *A, const void *B, uint64_t L, cudaStream_t st);
+
 // Enqueue c = a * b on `st` using `buf` (2 L words of device scratch).
 int enqueue_polymul(ntt_plan_s *pl, const void *a, size_t na, const void *b, size_t nb, void *c, void *buf,
                     cudaStream_t st);

@@ -106,6 +106,7 @@ __device__ __forceinline__ PassArgs<uint32_t> item_args(const UTask &t, const US
     a.ma = sg.ma;
     a.mb = sg.mb;
     a.p = t.p;
+    a.J = 0;  // lazy butterflies only
     a.rowptrs = t.rowptrs;
     a.nrows = t.rowptrs ? t.nrows : (1ull << (t.logL - sg.logR));
     return a;

@@ -74,6 +74,12 @@ static void check_one(const Consts<W> &c, uint64_t X, uint64_t Y, uint64_t p, in
             ey = mulmod(w, (X % p + p - Y % p) % p, p);
             lim = 2 * p;
             break;
+        case 7:  // Montgomery inverse (Algorithm 4 with Algorithm 5's product): [0,4p) -> [0,4p)
+            bfly_inv_mont(x, y, c.wm, c.J, c.p, c.p2);
+            ex = (X % p + mulmod(w, Y % p, p)) % p;
+            ey = (X % p + p - mulmod(w, Y % p, p)) % p;
+            lim = 4 * p;
+            break;
         case 6:  // fully reduced inverse: [0,p) -> [0,p)
             bfly_inv_ntl(x, y, c.w, c.wq, c.p);
             ex = (X + mulmod(w, Y, p)) % p;
@@ -117,7 +123,7 @@ static void check_one(const Consts<W> &c, uint64_t X, uint64_t Y, uint64_t p, in
 }
 
 static uint64_t in_limit(int which, uint64_t p) {
-    return which == 3 || which == 5 || which == 13 ? 2 * p : which == 4 || which == 14 ? 4 * p : p;
+    return which == 3 || which == 5 || which == 13 ? 2 * p : which == 4 || which == 7 || which == 14 ? 4 * p : p;
 }
 
 // Exhaustive at beta = 2^8.
@@ -125,8 +131,8 @@ static long long exhaustive8() {
     long long n = 0;
     for (uint64_t p = 3; p < 128; p++) {
         if (!isprime_u64(p)) continue;
-        for (int which : {2, 3, 4, 5, 6, 12, 13, 14, 16}) {
-            bool lazy = which == 3 || which == 4 || which == 5 || which == 13 || which == 14;
+        for (int which : {2, 3, 4, 5, 6, 7, 12, 13, 14, 16}) {
+            bool lazy = which == 3 || which == 4 || which == 5 || which == 7 || which == 13 || which == 14;
             if (lazy && p >= 64) continue;  // p < beta/4 (Algorithms 3-5)
             for (uint64_t w = 1; w < (which >= 12 ? 2 : p); w++) {
                 Consts<uint8_t> c = make<uint8_t>(p, w, 8);
@@ -150,7 +156,7 @@ static uint64_t rnd() {
 template <typename W>
 static long long sampled(uint64_t p, int bits, int samples) {
     long long n = 0;
-    for (int which : {2, 3, 4, 5, 6, 12, 13, 14, 16}) {
+    for (int which : {2, 3, 4, 5, 6, 7, 12, 13, 14, 16}) {
         uint64_t lim = in_limit(which, p);
         for (int s = 0; s < samples; s++) {
             uint64_t w = 1 + rnd() % (p - 1);

@@ -3,7 +3,8 @@ reduction (Section 3), through the C ABI.  Every input is seeded.
 
 Covered: every length 2^1 .. 2^16 (single and multi-pass schedules) with a
 ragged batch and padded stride; the 32-bit and 64-bit word paths; the lazy
-(Algorithms 3/4) and NTL-style (Algorithm 2) variants; forward and inverse
+(Algorithms 3/4), NTL-style (Algorithm 2) and Montgomery (Algorithm 5)
+variants; forward and inverse
 (Section 4); redundant inputs in [0,2p) / [0,4p); every allowed pass split at
 selected lengths; the full-size workloads (64 x 2^16, 2^20, 2^22 at 32 bits;
 16 x 2^20 and 2^24 at 64 bits) compared in full; argument errors."""
@@ -55,7 +56,7 @@ def pad_stride(L, wbytes, extra):
 
 @pytest.mark.parametrize("p", [P_NTT30, P_UNEVEN[0], P_NTT62])
 @pytest.mark.parametrize("logL", list(range(1, 17)))
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_forward_inverse_all_lengths(p, logL, variant):
     torch = require_gpu()
     L = 1 << logL
@@ -79,8 +80,10 @@ def test_forward_inverse_all_lengths(p, logL, variant):
 
 @pytest.mark.parametrize("p", [P_NTT30, P_NTT62])
 @pytest.mark.parametrize("logL", [3, 9, 13, 16])
-def test_redundant_inputs(p, logL):
-    """Algorithm 3 accepts [0,2p) and Algorithm 4 accepts [0,4p) on input."""
+@pytest.mark.parametrize("variant", [0, 2])
+def test_redundant_inputs(p, logL, variant):
+    """Algorithms 3 and 5 accept [0,2p), Algorithm 4 and its Montgomery
+    counterpart [0,4p) on input."""
     torch = require_gpu()
     L = 1 << logL
     o = orc()
@@ -88,10 +91,10 @@ def test_redundant_inputs(p, logL):
     plan = ntt.ntt_plan(p, w, L)
     dt = word_dtype(p)
     a = uniform_residues(300 + logL, 2 * L, 2 * p).astype(dt).reshape(2, L)
-    got = run(plan, a, False, None, 0, torch)
+    got = run(plan, a, False, None, variant, torch)
     assert np.array_equal(got.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64) % np.uint64(p)))
     y = uniform_residues(400 + logL, 2 * L, 4 * p).astype(dt).reshape(2, L)
-    got = run(plan, y, True, None, 0, torch)
+    got = run(plan, y, True, None, variant, torch)
     assert np.array_equal(got.astype(np.uint64), o.intt_ref(p, w, y.astype(np.uint64) % np.uint64(p)))
     plan.destroy()
 
@@ -106,7 +109,7 @@ SPLITS = {
 
 @pytest.mark.parametrize("p", [P_NTT30, P_NTT62])
 @pytest.mark.parametrize("logL,split", [(k, s) for k, v in SPLITS.items() for s in v])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_every_split(p, logL, split, variant):
     torch = require_gpu()
     L = 1 << logL
@@ -141,7 +144,7 @@ FULL = [
 
 
 @pytest.mark.parametrize("p,logL,batch", FULL)
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_full_size_workloads(p, logL, batch, variant):
     torch = require_gpu()
     L = 1 << logL

@@ -111,3 +111,43 @@ def test_golden_forward_L1024_regenerates(o):
     a = uniform_residues(seed, L, p)
     assert [int(v) for v in a] == g["input"]
     assert [int(v) for v in o.dft_naive(p, w, a)] == g["output"]
+
+
+def _schoolbook_limbs(a, b):
+    """Long multiplication limb by limb with explicit carries (base 2^32): an
+    algorithm independent of Python's big-integer product."""
+    out = [0] * (len(a) + len(b))
+    for i, ai in enumerate(a):
+        carry = 0
+        for j, bj in enumerate(b):
+            t = out[i + j] + int(ai) * int(bj) + carry
+            out[i + j] = t & 0xFFFFFFFF
+            carry = t >> 32
+        k = i + len(b)
+        while carry:
+            t = out[k] + carry
+            out[k] = t & 0xFFFFFFFF
+            carry = t >> 32
+            k += 1
+    return out
+
+
+@pytest.mark.parametrize("na,nb,seed", [(1, 1, 0), (1, 9, 1), (7, 3, 2), (33, 65, 3), (128, 5, 4)])
+def test_bigint_oracle_against_schoolbook(na, nb, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, 1 << 32, size=na, dtype=np.uint64).astype(np.uint32)
+    b = rng.integers(0, 1 << 32, size=nb, dtype=np.uint64).astype(np.uint32)
+    assert list(map(int, oracle.bigint_mul(a, b))) == _schoolbook_limbs(a, b)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 300])
+def test_bigint_oracle_closed_forms(n):
+    """(2^(32n) - 1)^2 = 2^(64n) - 2^(32n+1) + 1: limbs 1, 0.., then 0xFFFFFFFE,
+    0xFFFFFFFF..; and x * 1 = x, x * 0 = 0."""
+    ones = np.full(n, 0xFFFFFFFF, dtype=np.uint32)
+    sq = oracle.bigint_mul(ones, ones)
+    want = [1] + [0] * (n - 1) + [0xFFFFFFFE] + [0xFFFFFFFF] * (n - 1)
+    assert list(map(int, sq)) == want
+    x = np.arange(1, n + 1, dtype=np.uint32) * np.uint32(2654435761)
+    assert list(map(int, oracle.bigint_mul(x, np.array([1], dtype=np.uint32)))) == list(map(int, x)) + [0]
+    assert not oracle.bigint_mul(x, np.array([0], dtype=np.uint32)).any()
