@@ -184,7 +184,9 @@ int ntt_transform_host(ntt_plan_t plan, int inverse, void *h_data, size_t batch,
  * natural-order coefficients in [0, p) in the word type of p; c receives
  * na + nb - 1 words.  omega is the library's root for (p, L).  Plans are
  * cached per (device, p, L); device scratch of 2*L words is allocated per
- * call (stream-ordered) and released on the stream.  Asynchronous on `stream`.
+ * call (stream-ordered, from a library pool per device that keeps up to
+ * 4 GiB reserved between calls) and released on the stream.  Asynchronous on
+ * `stream`.
  * Errors: NTT_ERR_ARG (null, na or nb zero), NTT_ERR_LENGTH (L does not divide
  * p-1), NTT_ERR_MODULUS, NTT_ERR_ALIGN, NTT_ERR_NOMEM, NTT_ERR_CUDA. */
 int polymul_mod_p(uint64_t p, const void *d_a, size_t na, const void *d_b, size_t nb, void *d_c, void *stream);
@@ -232,7 +234,8 @@ int polymul_mod_p_noalloc(ntt_plan_t plan, const void *d_a, size_t na, const voi
  * (Garner's form), and their words summed with a parallel carry scan.
  * c receives na + nb limbs (the top one may be 0); a and b are not modified
  * and may not overlap c.  Limits: na + nb - 1 <= 2^23.  Device scratch of
- * 24 (nextpow2(na + nb - 1)) bytes comes from cudaMallocAsync on `stream`.
+ * 24 (nextpow2(na + nb - 1)) bytes comes stream-ordered from the same
+ * library pool as polymul_mod_p's.
  * Asynchronous on `stream`.
  * Errors: NTT_ERR_ARG (null pointer or zero length), NTT_ERR_RANGE, NTT_ERR_NOMEM,
  * NTT_ERR_CUDA. */

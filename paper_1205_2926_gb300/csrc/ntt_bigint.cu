@@ -186,7 +186,7 @@ extern "C" int bigint_mul(const uint32_t *a, size_t na, const uint32_t *b, size_
     const uint64_t nblocks = (nc + (uint64_t)kScanThreads * kChunk - 1) / ((uint64_t)kScanThreads * kChunk);
     uint32_t *buf = nullptr;
     const size_t bytes = 3 * 2 * L * sizeof(uint32_t) + nblocks * (sizeof(uint32_t) + 1) + 16;
-    cudaError_t e = cudaMallocAsync((void **)&buf, bytes, st);
+    cudaError_t e = scratch_alloc((void **)&buf, bytes, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "bigint scratch");
     int rc = NTT_OK;
     for (int i = 0; i < 3 && rc == NTT_OK; ++i) {

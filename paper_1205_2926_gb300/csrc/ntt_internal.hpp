@@ -108,6 +108,12 @@ bool split_allowed(int logL, int wbytes, int n, const int *logr);
 // Free the staging buffer, streams and events of ntt_transform_host.
 void release_host_pipeline(ntt_plan_s *plan);
 
+// Stream-ordered scratch for the library's own calls (polymul_mod_p,
+// bigint_mul): a memory pool per device that keeps up to 4 GiB reserved
+// between calls instead of returning it to the driver at every
+// synchronisation (re-mapping a large slab costs milliseconds).
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t st);
+
 // Record a CUDA failure for ntt_last_cuda_error(); returns NTT_ERR_CUDA.
 int cuda_fail(cudaError_t e, const char *where);
 

@@ -155,7 +155,7 @@ extern "C" int polymul_mod_p(uint64_t p, const void *d_a, size_t na, const void 
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     void *buf = nullptr;
-    cudaError_t e = cudaMallocAsync(&buf, 2 * L * wb, st);
+    cudaError_t e = scratch_alloc(&buf, 2 * L * wb, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "cudaMallocAsync");
     rc = enqueue_polymul(pl, d_a, na, d_b, nb, d_c, buf, st);
     e = cudaFreeAsync(buf, st);
