@@ -122,12 +122,7 @@ class ClockSampler:
 # of the current kernels (profiles/k_pass_u32_64x2p16_full.md), keyed by
 # workload and pass; passes without a capture report null.  The writes are 0:
 # the pass's output stays in the 129 MB L2 until it is evicted later.
-NCU_TRAFFIC = {
-    ("c2", "forward pass 0 of 64 x 2^16 (log2 R = 7)"): 17356288 + 0,
-    ("c2", "forward pass 1 of 64 x 2^16 (log2 R = 9)"): 16805376 + 0,
-    ("c2", "inverse pass 0 of 64 x 2^16 (log2 R = 9)"): 16810496 + 0,
-    ("c2", "inverse pass 1 of 64 x 2^16 (log2 R = 7)"): 17366528 + 0,
-}
+NCU_TRAFFIC = {}  # the kernels changed since the last capture: no figures until the next one
 
 
 def alu_peak_bfly(word_bytes, sm_mhz):
@@ -631,6 +626,54 @@ def run_probe():
             "unit": "butterflies/clk/SM", "higher_is_better": True, "config": {"workload": "probe"}, "probe": res}
 
 
+STEADY = {
+    "c2": [(P_NTT30, 20, 64), (P_NTT30, 22, 16), (P_NTT30, 16, 1024)],
+    "c3": [(P_NTT62, 20, 32), (P_NTT62, 24, 2)],
+}
+
+
+def steady_state(cases, torch, ntt, peak_gbs, K=20):
+    """The pass kernels at 256 MiB per pass (twice the L2, so every pass reads
+    and writes HBM): per pass and per whole forward+inverse transform, useful
+    bytes (one read and one write of every word per pass) over the CUDA-event
+    time of K back-to-back launches, against the measured HBM copy peak.  The
+    split is the library's own for that batch (autotuned, cached)."""
+    out = []
+    for p, l, b in cases:
+        L = 1 << l
+        w = 4 if p < (1 << 30) else 8
+        plan = ntt.ntt_plan(p, ntt.root_of_unity(p, L), L)
+        split = plan.autotune(b, use_cache=True)
+        a = batch_inputs(3, b, L, p)
+        t = torch.from_numpy(a.view(np.int32) if w == 4 else a.view(np.int64)).cuda()
+        passes, total_us = [], 0.0
+        for inv in (0, 1):
+            for k in range(len(split)):
+                for _ in range(3):
+                    ntt.ntt_execute_step(plan, inv, k, t, b)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(K):
+                    ntt.ntt_execute_step(plan, inv, k, t, b)
+                e1.record()
+                torch.cuda.synchronize()
+                us = e0.elapsed_time(e1) * 1e3 / K
+                total_us += us
+                gbs = 2 * b * L * w / (us * 1e-6) / 1e9
+                passes.append({"pass": f"{'inverse' if inv else 'forward'} {k}",
+                               "log2_R": (split[::-1] if inv else split)[k], "us": round(us, 1),
+                               "GBs": round(gbs), "frac": round(gbs / peak_gbs, 3)})
+        moved = 2 * len(split) * 2 * b * L * w
+        out.append({"workload": f"{b} x 2^{l}, {8 * w}-bit words ({b * L * w >> 20} MiB)", "split": split,
+                    "passes": passes, "fwd_inv_us": round(total_us, 1),
+                    "butterflies_per_s": 2 * b * (L // 2) * l / (total_us * 1e-6),
+                    "hbm_frac_of_transform": round(moved / (total_us * 1e-6) / 1e9 / peak_gbs, 3)})
+        del t
+        plan.destroy()
+    torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args, dist, rank, world):
     import torch
     import paper_1205_2926_gb300 as ntt
@@ -740,6 +783,9 @@ def run_ours(args, dist, rank, world):
         "graph": "timed steps are CUDA graph replays; kernel times from an eager pass with events",
         "clocks": clocks,
     }
+    if args.workload in STEADY:
+        line["steady_state"] = {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
+                                "cases": steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"])}
     if not args.no_serving and args.workload == "c2":
         line["polymul_serving"] = run_serving(args.serve_seconds, 20000.0, torch, ntt)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -279,6 +279,25 @@ int ntt_uneven_status(int *status);
  * (a prepared batch keeps no copy of these values). */
 int ntt_uneven_set_wait_budget(long long cycles, int stall_stage);
 
+/* Status word of the pass kernels on the current device (synchronous read):
+ * NTT_OK, or NTT_ERR_TIMEOUT when a pass kernel gave up waiting for one of
+ * its tile copies (64-bit column passes fetch tiles by tensor copies that
+ * complete on an mbarrier; every wait is bounded, after which the kernel
+ * records the timeout and returns instead of hanging; its output is then
+ * invalid).  reset != 0 clears the word after reading it.  Returns NTT_OK or
+ * NTT_ERR_ARG / NTT_ERR_CUDA. */
+int ntt_pass_status(int reset, int *status);
+
+/* Failure-detection hook for tests and operators: set the clock-cycle budget
+ * of each tile-copy wait of the pass kernels (default 2e9, about one second)
+ * and, with stall_bytes > 0 (a multiple of 16, at most 65536), make every
+ * tile copy expect that many bytes more than can ever arrive, so that its
+ * wait runs out and ntt_pass_status reports NTT_ERR_TIMEOUT instead of the
+ * kernel hanging.  stall_bytes = 0 restores normal waits.  Takes effect at
+ * the next launch; a captured CUDA graph keeps the values it was captured
+ * with. */
+int ntt_pass_set_wait_budget(long long cycles, unsigned int stall_bytes);
+
 /* -------------------------------------------------- polymul serving loop */
 
 /* A continuous-batching server of polynomial products mod p (the Section 1

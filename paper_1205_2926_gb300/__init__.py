@@ -181,6 +181,17 @@ def ntt_uneven_set_wait_budget(cycles: int, stall_stage: int = -1) -> None:
     check(_lib.load().ntt_uneven_set_wait_budget(cycles, stall_stage), "ntt_uneven_set_wait_budget")
 
 
+def ntt_pass_status(reset: bool = False) -> int:
+    """Status word of the pass kernels on the current device (NTT_OK or NTT_ERR_TIMEOUT)."""
+    s = ctypes.c_int()
+    check(_lib.load().ntt_pass_status(1 if reset else 0, ctypes.byref(s)), "ntt_pass_status")
+    return s.value
+
+
+def ntt_pass_set_wait_budget(cycles: int, stall_bytes: int = 0) -> None:
+    check(_lib.load().ntt_pass_set_wait_budget(cycles, stall_bytes), "ntt_pass_set_wait_budget")
+
+
 class Server:
     """Continuous-batching polymul server (ntt_server_*); host arrays in and out."""
 

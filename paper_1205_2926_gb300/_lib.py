@@ -70,6 +70,8 @@ _SIGNATURES = {
     "ntt_execute_uneven": (c_int, [ctypes.POINTER(Desc), c_size, c_void_p]),
     "ntt_uneven_status": (c_int, [ctypes.POINTER(c_int)]),
     "ntt_uneven_set_wait_budget": (c_int, [ctypes.c_longlong, c_int]),
+    "ntt_pass_status": (c_int, [c_int, ctypes.POINTER(c_int)]),
+    "ntt_pass_set_wait_budget": (c_int, [ctypes.c_longlong, ctypes.c_uint]),
     "ntt_server_create": (c_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(c_void_p)]),
     "ntt_server_submit": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_size, c_void_p,
                                   ctypes.POINTER(c_u64)]),

@@ -2,6 +2,7 @@
 // translation units (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,6 +84,10 @@ struct LaunchSpec {
     uint64_t nrows;
     unsigned grid;  // tiny kernel only
     size_t smem;    // dynamic shared memory of the launch
+    int *status;    // device status word of the pass kernels
+    long long wait_budget;  // clock cycles a pass kernel waits for one tile copy
+    uint32_t tx_extra;      // extra bytes each tile copy expects (a test hook; 0)
+    CUtensorMap map;  // column tiles by tensor copies (flag 8): the column view of the data
 };
 
 // Tile geometry of pass q of a plan for a batch (or, for a row pass over

@@ -26,28 +26,33 @@
 // are the same element of V independent sub-transforms, so they share every
 // twiddle:
 //   column pass: lanes are V adjacent columns (one 16-byte global chunk);
-//   row pass: lanes are V consecutive rows; the copy into shared memory
-//     transposes (one word per cp.async).
+//   row pass: lanes are V consecutive rows.
+// Each thread holds E = 8 vectors in registers and runs up to three
+// butterfly stages per round (radix-8 blocks); rounds exchange vectors
+// through shared memory.  The vector of row s sits at chunk
+// TV*(s + (s >> 3)) + tv (one padding chunk per eight), or TV*s + tv in
+// column tiles of TV = 8 vectors: in every round the eight threads of a
+// quarter-warp hit eight distinct bank groups, and the eight chunks of one
+// thread sit at compile-time offsets from one base.  Only the threads that
+// share a sub-tile synchronise between rounds (a warp, a named barrier or
+// the CTA).
+//
+// Data movement.  CTAs are persistent: each walks its tiles with stride
+// gridDim.x.  The first round of a pass loads its vectors straight from
+// global memory into registers (coalesced, through L2 only), except in
+// 64-bit column passes, which fetch the next tile into a second buffer
+// while computing the current one: by tensor copies (cp.async.bulk.tensor,
+// completion on an mbarrier) when tile rows are 128 bytes, else by cp.async.
 // The last round of every pass writes straight from registers to HBM:
 // 16-byte vectors in a column pass, eight consecutive words of each row in
 // the forward row pass, and in the inverse row pass word stores in which
 // neighbouring threads write neighbouring words of a row.
-// Each thread holds E = 8 vectors in registers and runs up to three
-// butterfly stages per round (radix-8 blocks); rounds exchange vectors
-// through shared memory.  The vector of row s sits at chunk
-// TV*(s + (s >> 3)) + tv (one padding chunk per eight): in every round the
-// eight threads of a quarter-warp hit eight distinct bank groups, and the
-// eight chunks of one thread sit at compile-time offsets from one base.
-//
-// Pipeline.  CTAs are persistent: each walks its tiles with stride gridDim.x
-// and prefetches the next tile with cp.async (16-byte global-to-shared
-// copies that bypass L1) into a second buffer while it computes the current
-// one, so HBM traffic overlaps the butterflies.
 //
 // Butterflies: Algorithm 3 / Algorithm 4 (lazy, redundant [0,2p) / [0,4p))
 // or Algorithm 2 / its fully reduced inverse (the NTL-style baseline).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -61,7 +66,7 @@ enum { DIR_FWD = 0, DIR_INV = 1 };
 // counterpart (lazy ranges, Montgomery's product; the twiddle pairs then hold
 // (W, beta W mod p)).
 enum { VAR_LAZY = 0, VAR_NTL = 1, VAR_MONT = 2 };
-enum { F_NORMALIZE = 1, F_MIDDLE = 2, F_MB = 4 };
+enum { F_NORMALIZE = 1, F_MIDDLE = 2, F_MB = 4, F_TMA = 8 };
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels
 
@@ -92,6 +97,9 @@ struct PassArgs {
     W J;                  // p^-1 mod beta (Montgomery variant)
     uint64_t nrows;       // row pass: number of rows (batch * L / R, or transforms)
     W *const *rowptrs;    // row pass over single-row transforms: address of each row (else null)
+    int *status;          // device status word: NTT_ERR_TIMEOUT when a tile copy never lands
+    long long wait_budget;  // clock cycles a CTA waits for one tile copy
+    uint32_t tx_extra;      // bytes each tile copy expects beyond its own (0; a test sets more)
 };
 
 // ------------------------------------------------------------- small helpers
@@ -364,7 +372,12 @@ template <typename W, int LOGR, bool ROW, int TVC = -1>
 struct Geo {
     static constexpr int LOGS = LOGR;                                // element-index bits
     static constexpr uint32_t NS = 1u << LOGS;                       // vectors per sub-transform
-    static constexpr uint32_t NSP = NS + (NS >> 3);                  // with padding
+    // Column tiles of 8 vectors per row (128 bytes) need no padding: the
+    // eight threads of a quarter-warp read one whole row.  Every other
+    // layout pads one chunk per eight rows.
+    static constexpr bool PAD = ROW || TVC != 3;
+    static constexpr uint32_t NSP = PAD ? NS + (NS >> 3) : NS;       // rows of one sub-tile, with padding
+    __host__ __device__ static constexpr uint32_t pidx(uint32_t s) { return PAD ? s + (s >> 3) : s; }
     using S = Sched<LOGS>;
 
     int logTV_, ltb, lbt;
@@ -429,9 +442,9 @@ __device__ __forceinline__ void tile_copy(const PassArgs<W> &a, const Geo<W, LOG
             uint32_t ct;
             uint32_t s = srow & ((1u << LOGR) - 1u);
             const W *g = geo.col_origin(a, t, ct) + s * S + cc * V;
-            uint4 *sp = buf + ((ti * G::NSP + s + (s >> 3)) << logTV) + cc;
+            uint4 *sp = buf + ((ti * G::NSP + G::pidx(s)) << logTV) + cc;
             const uint64_t gstep = rows_step * S;
-            const uint32_t sstep = (rows_step + rows_step / 8) << logTV;
+            const uint32_t sstep = G::pidx(rows_step) << logTV;
             for (; s < (1u << LOGR); s += rows_step, srow += rows_step) {
                 cp_async16(sp, g);
                 g += gstep;
@@ -517,7 +530,7 @@ __device__ __forceinline__ void unit_round(const PassArgs<W> &a, const Geo<W, LO
     } else {
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
+            const uint32_t cj = G::pidx((uint32_t)j << B0);
             rp[cj << logTV] = pack<W>(x[j]);
         }
     }
@@ -545,7 +558,7 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
             const uint32_t ti = u >> (G::LOGS - LE);
             const uint32_t lo = g & ((1u << B0) - 1u);
             const uint32_t s0 = ((g >> B0) << (B0 + LE)) | lo;
-            uint4 *rp = buf + ti * G::NSP + s0 + (s0 >> 3);
+            uint4 *rp = buf + ti * G::NSP + G::pidx(s0);
             const uint64_t row0 = ((uint64_t)tile * a.per_cta + ti) * V;
             W x[E][V];
 #pragma unroll
@@ -584,7 +597,7 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
             const uint32_t ti = u >> (logTV + G::LOGS - LE);
             const uint32_t lo = g & ((1u << B0) - 1u);
             const uint32_t s0 = ((g >> B0) << (B0 + LE)) | lo;
-            uint4 *rp = buf + ((ti * G::NSP + s0 + (s0 >> 3)) << logTV) + tv;
+            uint4 *rp = buf + ((ti * G::NSP + G::pidx(s0)) << logTV) + tv;
             const uint32_t t = tile * a.per_cta + ti;
             W x[E][V];
             if (t < geo.sub_total) {
@@ -610,14 +623,31 @@ __device__ __forceinline__ void tile_round(const PassArgs<W> &a, const Geo<W, LO
         const uint32_t ti = u >> (logTV + G::LOGS - LE);
         const uint32_t lo = g & ((1u << B0) - 1u);
         const uint32_t s0 = ((g >> B0) << (B0 + LE)) | lo;
-        uint4 *rp = buf + ((ti * G::NSP + s0 + (s0 >> 3)) << logTV) + tv;
+        uint4 *rp = buf + ((ti * G::NSP + G::pidx(s0)) << logTV) + tv;
         W x[E][V];
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const uint32_t cj = ((uint32_t)j << B0) + (((uint32_t)j << B0) >> 3);
+            const uint32_t cj = G::pidx((uint32_t)j << B0);
             unpack(rp[cj << logTV], x[j]);
         }
         unit_round<W, DIR, VAR, LOGR, ROW, TVC, RI>(a, geo, tile, rp, ti, tv, s0, lo, x);
+    }
+}
+
+// Barrier among the threads that share one sub-tile's shared memory: the
+// threads of sub-tile ti are the contiguous block [ti T, (ti + 1) T), T =
+// R TV / 8 (one unit each).  Whole CTA when T >= 256, the warp when T <= 32,
+// else a named barrier (ids 1 .. 8) over the T threads.
+template <typename W, int LOGR, bool ROW, int TVC>
+__device__ __forceinline__ void group_sync(const Geo<W, LOGR, ROW, TVC> &geo) {
+    const int logT = LOGR - 3 + geo.logTV();
+    if (logT >= 8) {
+        __syncthreads();
+    } else if (logT <= 5) {
+        __syncwarp();
+    } else {
+        const uint32_t id = 1u + (threadIdx.x >> logT), n = 1u << logT;
+        asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
     }
 }
 
@@ -626,7 +656,7 @@ __device__ __forceinline__ void tile_rounds(const PassArgs<W> &a, const Geo<W, L
                                             uint4 *buf) {
     tile_round<W, DIR, VAR, LOGR, ROW, TVC, RI>(a, geo, tile, buf);
     if constexpr (RI + 1 < Geo<W, LOGR, ROW, TVC>::S::NR) {
-        __syncthreads();
+        group_sync(geo);
         tile_rounds<W, DIR, VAR, LOGR, ROW, TVC, RI + 1>(a, geo, tile, buf);
     }
 }
@@ -668,6 +698,104 @@ __device__ __forceinline__ void tile_compute(const PassArgs<W> &a, uint32_t tile
     tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, buf);
 }
 
+// ---------------------------------------------------------------- TMA tiles
+//
+// Column passes whose tile rows are 128 bytes (8 vectors) can fetch a whole
+// sub-tile with tensor copies (cp.async.bulk.tensor) described by a 3-D map
+// {column S, row L/S, transform}: one copy of up to 256 rows x 128 bytes.
+// One thread issues them; completion is counted in bytes on an mbarrier per
+// buffer, so the next tile streams in while the CTA computes the current one.
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of the barrier, for at most `budget` clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > budget) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+template <typename W, int LOGR, bool ROW, int TVC>
+__device__ __forceinline__ void tma_tile(const PassArgs<W> &a, const Geo<W, LOGR, ROW, TVC> &geo,
+                                         const CUtensorMap *map, uint32_t tile, uint4 *buf, uint64_t *bar) {
+    using G = Geo<W, LOGR, ROW, TVC>;
+    constexpr uint32_t R = 1u << LOGR;
+    constexpr uint32_t BOX = R < 256 ? R : 256;
+    const int logTV = geo.logTV();
+    uint32_t n = 0;
+    for (uint32_t ti = 0; ti < (uint32_t)a.per_cta && tile * a.per_cta + ti < geo.sub_total; ++ti) ++n;
+    mbar_expect(bar, n * (R << logTV) * 16u + a.tx_extra);
+    for (uint32_t ti = 0; ti < n; ++ti) {
+        const uint32_t t = tile * a.per_cta + ti;
+        const uint32_t ct = t & ((1u << geo.ltb) - 1u);
+        const uint32_t blk = (t >> geo.ltb) & ((1u << geo.lbt) - 1u), b = t >> (geo.ltb + geo.lbt);
+        const int x = (int)(ct << (logTV + Lanes<W>::LOGV));
+#pragma unroll
+        for (uint32_t r0 = 0; r0 < R; r0 += BOX) {
+            const int y = (int)((blk << LOGR) + r0);
+            uint4 *dst = buf + ((ti * G::NSP + r0) << logTV);
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                "%4}], [%5];\n" ::"r"(smem_addr(dst)),
+                "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"((int)b), "r"(smem_addr(bar))
+                : "memory");
+        }
+    }
+}
+
+// One pass whose column tiles arrive by tensor copies, double buffered.  A
+// copy that has not landed within a.wait_budget cycles (about a second by
+// default) sets NTT_ERR_TIMEOUT in the status word; the CTA then waits (also
+// bounded) for its other copy in flight and stops.
+template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
+__device__ __forceinline__ void pass_loop_tma(const PassArgs<W> &a, const CUtensorMap *map, uint4 *sm) {
+    const Geo<W, LOGR, ROW, TVC> geo(a);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * a.buf_chunks);  // after the two buffers
+    const long long kBudget = a.wait_budget;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0]);
+        mbar_init(&bars[1]);
+        fence_proxy_async();
+    }
+    __syncthreads();
+    uint32_t tile = blockIdx.x;
+    if (threadIdx.x == 0 && tile < a.ntiles) tma_tile<W, LOGR, ROW, TVC>(a, geo, map, tile, sm, &bars[0]);
+    for (uint32_t it = 0; tile < a.ntiles; tile += gridDim.x, ++it) {
+        uint4 *cur = (it & 1) ? sm + a.buf_chunks : sm;
+        uint4 *nxt = (it & 1) ? sm : sm + a.buf_chunks;
+        const uint32_t next = tile + gridDim.x;
+        const bool more = next < a.ntiles;
+        if (threadIdx.x == 0 && more) tma_tile<W, LOGR, ROW, TVC>(a, geo, map, next, nxt, &bars[(it + 1) & 1]);
+        const bool ok = mbar_wait(&bars[it & 1], (it >> 1) & 1, kBudget);
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(a.status, NTT_ERR_TIMEOUT);
+                if (more) mbar_wait(&bars[(it + 1) & 1], ((it + 1) >> 1) & 1, kBudget);
+            }
+            return;
+        }
+        tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, cur);
+        fence_proxy_async();  // this tile's shared-memory writes before a later copy overwrites them
+        __syncthreads();
+    }
+}
+
 // One pass over a batch: persistent CTAs with cp.async double buffering.
 template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
 __device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
@@ -681,12 +809,17 @@ __device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
         uint4 *cur = (PF && (it & 1)) ? sm + a.buf_chunks : sm;
         uint4 *nxt = (PF && (it & 1)) ? sm : sm + a.buf_chunks;
         const uint32_t next = tile + gridDim.x;
-        if (next < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, next, nxt);
-        cp_async_commit();
-        cp_async_wait<1>();
-        __syncthreads();
+        if (PF) {
+            if (next < a.ntiles) tile_copy<W, LOGR, ROW>(a, geo, next, nxt);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncthreads();
+        }
         tile_rounds<W, DIR, VAR, LOGR, ROW, TVC>(a, geo, tile, cur);
-        __syncthreads();
+        if (PF)
+            __syncthreads();
+        else
+            group_sync(geo);  // this tile's last reads before the next tile's first writes
     }
     cp_async_wait<0>();
 }
@@ -700,9 +833,16 @@ struct Occupancy {
 };
 
 template <typename W, int DIR, int VAR, int LOGR, bool ROW>
-__global__ void __launch_bounds__(kThreads, (Occupancy<W, LOGR>::CTAS)) k_pass(const PassArgs<W> a) {
+__global__ void __launch_bounds__(kThreads, (Occupancy<W, LOGR>::CTAS))
+    k_pass(const PassArgs<W> a, const __grid_constant__ CUtensorMap map) {
     extern __shared__ uint4 sm[];
     constexpr int TVF = ColWidth<LOGR, ColTileLog<W, LOGR>::MAX>::LOGTV;
+    if constexpr (!ROW && TVF == 3 && sizeof(W) == 8) {  // tensor copies: 64-bit column passes
+        if (a.flags & F_TMA) {
+            pass_loop_tma<W, DIR, VAR, LOGR, ROW, 3>(a, &map, sm);
+            return;
+        }
+    }
     if (ROW || a.logTV == TVF)
         pass_loop<W, DIR, VAR, LOGR, ROW, ROW ? 0 : TVF>(a, sm);
     else

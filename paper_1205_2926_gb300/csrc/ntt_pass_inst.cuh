@@ -31,6 +31,9 @@ static PassArgs<W> to_args(const LaunchSpec &s) {
     a.J = (W)s.J;
     a.nrows = s.nrows;
     a.rowptrs = nullptr;
+    a.status = s.status;
+    a.wait_budget = s.wait_budget;
+    a.tx_extra = s.tx_extra;
     return a;
 }
 
@@ -81,7 +84,7 @@ static cudaError_t launch_k(const LaunchSpec &s, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const uint64_t slots = (uint64_t)per_sm * sms;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(s.ntiles, slots));
-    kern<<<grid, kThreads, s.smem, st>>>(to_args<W>(s));
+    kern<<<grid, kThreads, s.smem, st>>>(to_args<W>(s), s.map);
     return cudaGetLastError();
 }
 

@@ -297,3 +297,57 @@ def test_library_number_theory_matches_oracle():
         for L in (2, 1024, 1 << 16):
             assert ntt.root_of_unity(p, L) == o.root_of_unity(p, L)
     assert ntt.find_prime(1 << 61, 24) == P_NTT62
+
+
+TMA_REF = {}
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("split,extra", [([8, 8], 0), ([6, 10], 0), ([7, 5, 4], 2)])
+def test_tensor_copy_column_tiles(split, extra, variant):
+    """64-bit column passes with 128-byte tile rows fetch their tiles by tensor
+    copies (cp.async.bulk.tensor); 40 transforms keep those tiles at full
+    width, and a padded stride exercises the map's transform dimension."""
+    torch = require_gpu()
+    o = orc()
+    p, L, batch = P_NTT62, 1 << 16, 40
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    plan.set_split(split)
+    a = batch_inputs(902, batch, L, p)  # one input for every split: the oracle runs once
+    if "ref" not in TMA_REF:
+        TMA_REF["ref"] = (o.ntt_ref(p, w, a.astype(np.uint64)), o.intt_ref(p, w, a.astype(np.uint64)))
+    fwd, inv = TMA_REF["ref"]
+    stride = pad_stride(L, 8, extra) if extra else None
+    assert ntt.ntt_pass_status(reset=True) == 0
+    assert np.array_equal(run(plan, a, False, stride, variant, torch).astype(np.uint64), fwd)
+    assert np.array_equal(run(plan, a, True, stride, variant, torch).astype(np.uint64), inv)
+    assert ntt.ntt_pass_status() == 0
+    plan.destroy()
+
+
+def test_tile_copy_wait_times_out_and_recovers():
+    """Tile copies that never complete (the test hook makes each expect 16 bytes
+    that never arrive) end the pass with NTT_ERR_TIMEOUT after the wait budget
+    instead of hanging; the next launch with normal waits is exact."""
+    torch = require_gpu()
+    o = orc()
+    p, L, batch = P_NTT62, 1 << 16, 40
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    plan.set_split([8, 8])
+    a = batch_inputs(911, batch, L, p)
+    ntt.ntt_pass_status(reset=True)
+    try:
+        ntt.ntt_pass_set_wait_budget(2_000_000, stall_bytes=16)  # about 1 ms per wait
+        run(plan, a, False, None, 0, torch)
+        assert ntt.ntt_pass_status(reset=True) == -7
+    finally:
+        ntt.ntt_pass_set_wait_budget(2_000_000_000, 0)
+    got = run(plan, a, False, None, 0, torch)
+    assert ntt.ntt_pass_status() == 0
+    assert np.array_equal(got.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64)))
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_pass_set_wait_budget(0, 0)
+    assert e.value.code == -4
+    plan.destroy()
