@@ -784,8 +784,11 @@ def run_ours(args, dist, rank, world):
         "clocks": clocks,
     }
     if args.workload in STEADY:
-        line["steady_state"] = {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
-                                "cases": steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"])}
+        try:
+            line["steady_state"] = {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
+                                    "cases": steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"])}
+        except Exception as e:  # a report of its own; the headline above stands
+            line["steady_state"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_serving and args.workload == "c2":
         line["polymul_serving"] = run_serving(args.serve_seconds, 20000.0, torch, ntt)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
