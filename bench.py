@@ -122,7 +122,12 @@ class ClockSampler:
 # of the current kernels (profiles/k_pass_u32_64x2p16_full.md), keyed by
 # workload and pass; passes without a capture report null.  The writes are 0:
 # the pass's output stays in the 129 MB L2 until it is evicted later.
-NCU_TRAFFIC = {}  # the kernels changed since the last capture: no figures until the next one
+NCU_TRAFFIC = {
+    ("c2", "forward pass 0 of 64 x 2^16 (log2 R = 7)"): 17356800 + 0,
+    ("c2", "forward pass 1 of 64 x 2^16 (log2 R = 9)"): 16805376 + 0,
+    ("c2", "inverse pass 0 of 64 x 2^16 (log2 R = 9)"): 16810496 + 0,
+    ("c2", "inverse pass 1 of 64 x 2^16 (log2 R = 7)"): 17366784 + 0,
+}
 
 
 def alu_peak_bfly(word_bytes, sm_mhz):
