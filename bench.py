@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures
+import gc
 import json
 import math
 import os
@@ -514,22 +515,34 @@ def run_serving(seconds, rate, torch, ntt, seed=5, max_log=20.0):
         sv.submit(base, m, base, m, rbase)
     sv.drain(-1)
     sv.reset_stats()
+    # the submission loop replays the trace from plain lists, with Python's
+    # garbage collector paused: a collection pass (tens of ms with this many
+    # live objects) would hold back submissions and then release them as one
+    # burst, which the latency of the burst would show instead of the server's
+    t_arr = [r["t_arrive_s"] for r in trace]
+    nas = [r["na"] for r in trace]
+    nbs = [r["nb"] for r in trace]
+    a_ptr = [base + 4 * int(x) for x in offs[:, 0]]
+    b_ptr = [base + 4 * int(x) for x in offs[:, 1]]
     rpos = 0
     load_before = os.getloadavg()[0]
+    gc_was = gc.isenabled()
+    gc.disable()
     t_start = time.perf_counter()
     refused = 0
-    for i, r in enumerate(trace):
-        target = t_start + r["t_arrive_s"]
+    for i in range(n):
+        target = t_start + t_arr[i]
         while time.perf_counter() < target:
             pass
-        out_words = r["na"] + r["nb"] - 1
+        out_words = nas[i] + nbs[i] - 1
         if rpos + out_words > ring_words:
             rpos = 0
-        rc, _ = sv.submit(base + 4 * int(offs[i, 0]), r["na"], base + 4 * int(offs[i, 1]), r["nb"],
-                          rbase + 4 * rpos)
+        rc, _ = sv.submit(a_ptr[i], nas[i], b_ptr[i], nbs[i], rbase + 4 * rpos)
         refused += rc != 0
         rpos += out_words
     t_sub = time.perf_counter() - t_start
+    if gc_was:
+        gc.enable()
     load_after = os.getloadavg()[0]
     sv.drain(-1)
     st = sv.stats()
@@ -539,6 +552,7 @@ def run_serving(seconds, rate, torch, ntt, seed=5, max_log=20.0):
             "mean_ms": st.mean_us / 1e3, "max_ms": st.max_us / 1e3,
             "throughput_req_per_s": st.completed / st.wall_s if st.wall_s else None,
             "butterflies_per_s": st.butterflies / st.wall_s if st.wall_s else None, "batches": int(st.batches),
+            "direct_batches": int(st.direct_batches),
             "host_load_1min": {"before": load_before, "after": load_after}}
 
 
@@ -788,7 +802,7 @@ def run_ours(args, dist, rank, world):
         "graph": "timed steps are CUDA graph replays; kernel times from an eager pass with events",
         "clocks": clocks,
     }
-    if args.workload in STEADY:
+    if args.workload in STEADY and not args.no_steady_state:
         try:
             line["steady_state"] = {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
                                     "cases": steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"])}
@@ -897,11 +911,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="serving run length (default: 60 s for --workload c5, 2 s inside the default bench)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-steady-state", action="store_true", help="skip the 256 MiB per-pass report")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.serve_seconds is None:
+        args.serve_seconds = 60.0 if args.workload == "c5" else 2.0
     if "NTT_AUTOTUNE_CACHE" not in os.environ:
         # start from the pass splits tuned on this GPU model (shipped with the
         # package); a shape or GPU it lacks is tuned at run time into the copy

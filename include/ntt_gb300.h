@@ -309,7 +309,14 @@ int ntt_pass_set_wait_budget(long long cycles, unsigned int stall_bytes);
  * least outstanding work (butterflies of its running batches).  Requests
  * arriving while batches run are admitted as memory frees up, and their
  * batches overlap with the running ones on the device.  Each result is the
- * same as polymul_mod_p on that request alone. */
+ * same as polymul_mod_p on that request alone.
+ * Host buffers: when both operands and the result of every request of a
+ * batch are in page-locked memory (cudaHostAlloc, cudaHostRegister, torch
+ * pin_memory), kernels gather the operands into the device slab and scatter
+ * the results back through unified addressing, with no per-request copy
+ * call; otherwise each operand and result is one cudaMemcpyAsync.  The
+ * server's memory pool maps min(mem_budget_bytes, 4 GiB) at creation and
+ * keeps up to mem_budget_bytes mapped between batches. */
 typedef struct ntt_server_s *ntt_server_t;
 
 typedef struct {
@@ -325,6 +332,9 @@ typedef struct {
     double butterflies;                      /* transform butterflies of completed requests */
     double p50_us, p99_us, mean_us, max_us;  /* submit-to-result latency of completed requests */
     double wall_s;                           /* first submit to last completion */
+    uint64_t direct_batches;                 /* batches whose operands and results were all in
+                                                page-locked host memory: gathered and scattered
+                                                by kernels, with no per-request copy calls */
 } ntt_server_stats_t;
 
 /* Start a server on the current device.  Errors: NTT_ERR_ARG, NTT_ERR_MODULUS,

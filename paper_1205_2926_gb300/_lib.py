@@ -40,7 +40,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("completed", c_u64), ("refused", c_u64), ("cancelled", c_u64), ("failed", c_u64),
                 ("batches", c_u64), ("butterflies", ctypes.c_double), ("p50_us", ctypes.c_double),
                 ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
-                ("wall_s", ctypes.c_double)]
+                ("wall_s", ctypes.c_double), ("direct_batches", c_u64)]
 
 
 class Desc(ctypes.Structure):

@@ -7,9 +7,15 @@
 // each group as one batch on the CUDA stream with the least outstanding work
 // (butterflies of the batches still running on it), so that small requests
 // do not queue behind a large one:
-//   zero the slab, copy operands in, forward transforms (2n vectors),
-//   pointwise product times L^-1, inverse transforms (n vectors), copy the
-//   na+nb-1 result words of each request straight to its host buffer.
+//   gather the operands into a zero-padded slab, forward transforms (2n
+//   vectors), pointwise product times L^-1, inverse transforms (n vectors),
+//   scatter the na+nb-1 result words of each request to its host buffer.
+// Operands and results in page-locked host memory are read and written by
+// the gather and scatter kernels themselves (the device reaches them
+// through unified addressing), so a batch costs a fixed handful of CUDA
+// calls whatever its size; other host memory goes through one copy per
+// operand and result.  The scheduler releases the server lock while it
+// issues a batch, so submitters never wait for the launches.
 // Requests that arrive while batches are on the GPU are admitted as soon as
 // memory frees up, into new batches on other streams, so their work overlaps
 // with the running ones.  Plans and twiddle tables stay resident on the
@@ -44,12 +50,45 @@ __global__ void k_pointwise_batch(W *__restrict__ A, const W *__restrict__ B, ui
     }
 }
 
+// Gather / scatter between the host buffers of up to kGather requests and
+// the slab: blockIdx.y is the request, blockIdx.z the operand (gather).
+constexpr int kGather = 32;
+struct GatherTable {
+    const void *a[kGather];
+    const void *b[kGather];
+    void *c[kGather];
+    uint32_t na[kGather], nb[kGather];
+};
+
+template <typename W>
+__global__ void k_gather(const GatherTable t, W *__restrict__ slab, uint64_t L, uint64_t row_a, uint64_t row_b) {
+    const int r = blockIdx.y;
+    const bool second = blockIdx.z != 0;
+    const W *__restrict__ src = static_cast<const W *>(second ? t.b[r] : t.a[r]);
+    const uint64_t cnt = second ? t.nb[r] : t.na[r];
+    W *__restrict__ dst = slab + ((second ? row_b : row_a) + r) * L;
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < L; j += (uint64_t)gridDim.x * blockDim.x)
+        dst[j] = j < cnt ? src[j] : (W)0;
+}
+
+template <typename W>
+__global__ void k_scatter(const GatherTable t, const W *__restrict__ slab, uint64_t L, uint64_t row0) {
+    const int r = blockIdx.y;
+    const uint64_t cnt = (uint64_t)t.na[r] + t.nb[r] - 1;
+    const W *__restrict__ src = slab + (row0 + r) * L;
+    W *__restrict__ dst = static_cast<W *>(t.c[r]);
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cnt; j += (uint64_t)gridDim.x * blockDim.x)
+        dst[j] = src[j];
+}
+
 using Clock = std::chrono::steady_clock;
 
 struct Request {
     uint64_t id;
     const void *a, *b;
     void *c;
+    const void *da = nullptr, *db = nullptr;  // device views of page-locked operands (else null)
+    void *dc = nullptr;                       // device view of a page-locked result buffer (else null)
     size_t na, nb;
     uint64_t L;
     Clock::time_point t_submit, t_done;
@@ -65,6 +104,7 @@ struct Batch {
     int stream = 0;
     int status = NTT_OK;
     double work = 0;  // butterflies of the batch (stream load balancing)
+    bool direct = false;  // operands gathered and results scattered by kernels
 };
 
 }  // namespace ntt
@@ -83,12 +123,13 @@ struct ntt_server_s {
     std::unordered_map<uint64_t, ntt::Request> reqs;
     std::vector<ntt::Batch> inflight;
     size_t inflight_bytes = 0;
+    int launching = 0;  // batches being issued with the lock released
     uint64_t next_id = 1;
     bool stop = false;
     int fail_next = 0;
     // statistics
     std::vector<double> lat_us;
-    uint64_t n_done = 0, n_refused = 0, n_cancelled = 0, n_failed = 0, n_batches = 0;
+    uint64_t n_done = 0, n_refused = 0, n_cancelled = 0, n_failed = 0, n_batches = 0, n_direct = 0;
     double butterflies = 0;
     ntt::Clock::time_point t_first, t_last;
     bool any = false;
@@ -103,7 +144,7 @@ static uint64_t bfly_count(uint64_t L) {
     return 3 * l * (L / 2);  // two forward transforms and one inverse
 }
 
-// Launch one batch (scheduler thread, server lock held).
+// Launch one batch (scheduler thread, server lock released).
 template <typename W>
 static int launch_batch_t(ntt_server_s *sv, Batch &bt, const std::vector<Request *> &rs, cudaStream_t st) {
     ntt_plan_s *pl = bt.plan;
@@ -112,13 +153,34 @@ static int launch_batch_t(ntt_server_s *sv, Batch &bt, const std::vector<Request
     cudaError_t e = cudaMallocFromPoolAsync(&bt.slab, bt.bytes, sv->pool, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "server slab");
     W *slab = (W *)bt.slab;
-    e = cudaMemsetAsync(slab, 0, bt.bytes, st);
-    if (e != cudaSuccess) return cuda_fail(e, "server memset");
-    for (uint64_t i = 0; i < n; ++i) {
-        e = cudaMemcpyAsync(slab + i * L, rs[i]->a, rs[i]->na * wb, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(slab + (n + i) * L, rs[i]->b, rs[i]->nb * wb, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(e, "server H2D");
+    bool direct = true;  // every operand and result buffer reachable from the device
+    for (const Request *r : rs) direct = direct && r->da && r->db && r->dc;
+    bt.direct = direct;
+    const unsigned gx = (unsigned)std::min<uint64_t>((L + 255) / 256, 64);
+    if (direct) {
+        for (uint64_t i0 = 0; i0 < n; i0 += kGather) {
+            const int m = (int)std::min<uint64_t>(kGather, n - i0);
+            GatherTable t;
+            for (int j = 0; j < m; ++j) {
+                t.a[j] = rs[i0 + j]->da;
+                t.b[j] = rs[i0 + j]->db;
+                t.c[j] = rs[i0 + j]->dc;
+                t.na[j] = (uint32_t)rs[i0 + j]->na;
+                t.nb[j] = (uint32_t)rs[i0 + j]->nb;
+            }
+            k_gather<W><<<dim3(gx, m, 2), 256, 0, st>>>(t, slab, L, i0, n + i0);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "server gather");
+    } else {
+        e = cudaMemsetAsync(slab, 0, bt.bytes, st);
+        if (e != cudaSuccess) return cuda_fail(e, "server memset");
+        for (uint64_t i = 0; i < n; ++i) {
+            e = cudaMemcpyAsync(slab + i * L, rs[i]->a, rs[i]->na * wb, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(slab + (n + i) * L, rs[i]->b, rs[i]->nb * wb, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return cuda_fail(e, "server H2D");
+        }
     }
     int rc = enqueue_transform(pl, 0, slab, 2 * n, L, st);
     if (rc) return rc;
@@ -134,9 +196,27 @@ static int launch_batch_t(ntt_server_s *sv, Batch &bt, const std::vector<Request
     if (e != cudaSuccess) return cuda_fail(e, "server pointwise");
     rc = enqueue_transform(pl, 1, slab, n, L, st);
     if (rc) return rc;
-    for (uint64_t i = 0; i < n; ++i) {
-        e = cudaMemcpyAsync(rs[i]->c, slab + i * L, (rs[i]->na + rs[i]->nb - 1) * wb, cudaMemcpyDeviceToHost, st);
-        if (e != cudaSuccess) return cuda_fail(e, "server D2H");
+    if (direct) {
+        for (uint64_t i0 = 0; i0 < n; i0 += kGather) {
+            const int m = (int)std::min<uint64_t>(kGather, n - i0);
+            GatherTable t;
+            for (int j = 0; j < m; ++j) {
+                t.a[j] = rs[i0 + j]->da;
+                t.b[j] = rs[i0 + j]->db;
+                t.c[j] = rs[i0 + j]->dc;
+                t.na[j] = (uint32_t)rs[i0 + j]->na;
+                t.nb[j] = (uint32_t)rs[i0 + j]->nb;
+            }
+            k_scatter<W><<<dim3(gx, m, 1), 256, 0, st>>>(t, slab, L, i0);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "server scatter");
+    } else {
+        for (uint64_t i = 0; i < n; ++i) {
+            e = cudaMemcpyAsync(rs[i]->c, slab + i * L, (rs[i]->na + rs[i]->nb - 1) * wb, cudaMemcpyDeviceToHost,
+                                st);
+            if (e != cudaSuccess) return cuda_fail(e, "server D2H");
+        }
     }
     e = cudaFreeAsync(bt.slab, st);
     bt.slab = nullptr;
@@ -188,7 +268,7 @@ static void scheduler(ntt_server_s *sv) {
             progressed = true;
         }
         if (progressed) sv->done_cv.notify_all();
-        if (sv->stop && sv->queue.empty() && sv->inflight.empty()) break;
+        if (sv->stop && sv->queue.empty() && sv->inflight.empty()) break;  // (launching is 0 here)
         // 2. admission in FIFO order while memory allows
         std::map<uint64_t, std::vector<uint64_t>> by_len;
         size_t admitted_bytes = 0;
@@ -229,8 +309,15 @@ static void scheduler(ntt_server_s *sv) {
                 rc = NTT_ERR_FAILED;  // host-side failure injection
             }
             if (rc == NTT_OK) {
+                // issue the batch without the lock: submitters go on queueing
+                // meanwhile (admitted requests are neither cancelled nor
+                // erased, and the request map keeps their addresses)
                 cudaStream_t st = sv->streams[bt.stream];
+                sv->launching++;
+                lk.unlock();
                 rc = sv->wbytes == 4 ? launch_batch_t<uint32_t>(sv, bt, rs, st) : launch_batch_t<uint64_t>(sv, bt, rs, st);
+                lk.lock();
+                sv->launching--;
             }
             if (rc != NTT_OK) {
                 // this batch fails; the others are unaffected
@@ -243,6 +330,7 @@ static void scheduler(ntt_server_s *sv) {
                 continue;
             }
             sv->n_batches++;
+            sv->n_direct += bt.direct ? 1 : 0;
             sv->inflight_bytes += bt.bytes;
             sv->stream_work[bt.stream] += bt.work;
             sv->inflight.push_back(bt);
@@ -318,9 +406,33 @@ int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out) {
             return cuda_fail(e, "server pool");
         }
     }
+    {
+        // map the pool's memory up front (the budget, at most 4 GiB): batches
+        // then never wait for the pool to grow while requests are served
+        void *p = nullptr;
+        const size_t reserve = std::min<size_t>(cfg->mem_budget_bytes, (size_t)4 << 30);
+        if (cudaMallocFromPoolAsync(&p, reserve, sv->pool, sv->streams[0]) == cudaSuccess) {
+            cudaFreeAsync(p, sv->streams[0]);
+            cudaStreamSynchronize(sv->streams[0]);
+        }
+        cudaGetLastError();  // a reservation that does not fit is not an error
+    }
     sv->worker = std::thread(scheduler, sv);
     *out = sv;
     return NTT_OK;
+}
+
+// Device view of a host buffer: page-locked (registered or cudaHostAlloc)
+// memory is reachable from the server's device at attr.devicePointer; any
+// other memory gives null (the batch then copies it).
+static void *device_view(const void *p, int device) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return (at.device == device || at.device < 0) ? at.devicePointer : nullptr;
 }
 
 int ntt_server_submit(ntt_server_t sv, const void *h_a, size_t na, const void *h_b, size_t nb, void *h_c,
@@ -328,8 +440,21 @@ int ntt_server_submit(ntt_server_t sv, const void *h_a, size_t na, const void *h
     if (!sv || !h_a || !h_b || !h_c || !req_id) return NTT_ERR_ARG;
     uint64_t L = 0;
     int rc = polymul_validate(sv->cfg.p, na, nb, &L);
+    void *da = nullptr, *db = nullptr, *dc = nullptr;
+    if (rc == NTT_OK) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != sv->device) cudaSetDevice(sv->device);
+        da = device_view(h_a, sv->device);
+        db = da ? device_view(h_b, sv->device) : nullptr;
+        dc = db ? device_view(h_c, sv->device) : nullptr;
+        if (cur >= 0 && cur != sv->device) cudaSetDevice(cur);
+    }
     std::lock_guard<std::mutex> lk(sv->mu);
     Request r;
+    r.da = da;
+    r.db = db;
+    r.dc = dc;
     r.id = sv->next_id++;
     r.a = h_a;
     r.b = h_b;
@@ -397,7 +522,7 @@ int ntt_server_cancel(ntt_server_t sv, uint64_t id) {
 int ntt_server_drain(ntt_server_t sv, int timeout_ms) {
     if (!sv) return NTT_ERR_ARG;
     std::unique_lock<std::mutex> lk(sv->mu);
-    auto idle = [sv] { return sv->queue.empty() && sv->inflight.empty(); };
+    auto idle = [sv] { return sv->queue.empty() && sv->inflight.empty() && sv->launching == 0; };
     if (timeout_ms < 0) {
         sv->done_cv.wait(lk, idle);
         return NTT_OK;
@@ -414,6 +539,7 @@ int ntt_server_stats(ntt_server_t sv, ntt_server_stats_t *out) {
     out->cancelled = sv->n_cancelled;
     out->failed = sv->n_failed;
     out->batches = sv->n_batches;
+    out->direct_batches = sv->n_direct;
     out->butterflies = sv->butterflies;
     std::vector<double> v = sv->lat_us;
     if (!v.empty()) {
@@ -434,7 +560,7 @@ int ntt_server_reset_stats(ntt_server_t sv) {
     if (!sv) return NTT_ERR_ARG;
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->lat_us.clear();
-    sv->n_done = sv->n_refused = sv->n_cancelled = sv->n_failed = sv->n_batches = 0;
+    sv->n_done = sv->n_refused = sv->n_cancelled = sv->n_failed = sv->n_batches = sv->n_direct = 0;
     sv->butterflies = 0;
     sv->any = false;
     for (auto it = sv->reqs.begin(); it != sv->reqs.end();) {

@@ -106,3 +106,51 @@ def test_cancel_queued_and_injected_failure():
         assert sum(s == 0 for s in statuses) == len(ids) - 1 - len(cancelled)
     finally:
         sv.destroy()
+
+
+def test_page_locked_buffers_gathered_by_kernels():
+    """Operands and results in page-locked host memory are gathered into the
+    slab and scattered back by kernels (no per-request copy calls); each result
+    equals the oracle's product and the one from pageable buffers, and a batch
+    that mixes page-locked and pageable requests takes the copy path."""
+    torch = require_gpu()
+    reqs = make_requests(40, seed=33)
+    sv = ntt.Server(P_NTT30, max_coeffs=1 << 15, mem_budget_bytes=256 << 20, n_streams=4)
+    try:
+        pinned = []
+        for a, b in reqs:
+            ta = torch.from_numpy(a.view(np.int32)).pin_memory()
+            tb = torch.from_numpy(b.view(np.int32)).pin_memory()
+            tc = torch.zeros(a.size + b.size - 1, dtype=torch.int32).pin_memory()
+            pinned.append((ta, tb, tc))
+        ids = []
+        for ta, tb, tc in pinned:
+            rc, rid = sv.submit(ta.data_ptr(), ta.numel(), tb.data_ptr(), tb.numel(), tc.data_ptr())
+            assert rc == 0
+            ids.append(rid)
+        assert sv.drain(60_000) == 0
+        st = sv.stats()
+        assert st.completed == len(reqs) and st.failed == 0
+        assert st.direct_batches == st.batches > 0
+        for (a, b), (_, _, tc) in zip(reqs, pinned):
+            assert np.array_equal(tc.numpy().view(np.uint32).astype(np.uint64), expected(a, b))
+        # the same requests from pageable memory: copy path, identical results
+        sv.reset_stats()
+        outs = [np.zeros(a.size + b.size - 1, dtype=np.uint32) for a, b in reqs]
+        for (a, b), c in zip(reqs, outs):
+            assert sv.submit(a.ctypes.data, a.size, b.ctypes.data, b.size, c.ctypes.data)[0] == 0
+        assert sv.drain(60_000) == 0
+        st = sv.stats()
+        assert st.direct_batches == 0 and st.completed == len(reqs)
+        for c, (_, _, tc) in zip(outs, pinned):
+            assert np.array_equal(c, tc.numpy().view(np.uint32))
+        # page-locked operands with a pageable result buffer: copy path
+        sv.reset_stats()
+        ta, tb, _ = pinned[0]
+        c = np.zeros(ta.numel() + tb.numel() - 1, dtype=np.uint32)
+        rc, rid = sv.submit(ta.data_ptr(), ta.numel(), tb.data_ptr(), tb.numel(), c.ctypes.data)
+        assert rc == 0 and sv.wait(rid, 60_000) == 0
+        assert sv.stats().direct_batches == 0
+        assert np.array_equal(c, outs[0])
+    finally:
+        sv.destroy()
