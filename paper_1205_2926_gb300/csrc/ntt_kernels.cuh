@@ -408,10 +408,11 @@ struct Geo {
     }
 };
 
-// Which passes prefetch their tiles into shared memory with cp.async (double
-// buffered) and which let their first round load straight from global memory
-// into registers: the direct load is faster for every 32-bit pass and for
-// 64-bit row passes (measured); 64-bit column passes keep the prefetch.
+// Which passes prefetch their next tile into a second shared buffer (by
+// tensor copies when tile rows are 128 bytes and the host enabled them, else
+// by cp.async) and which let their first round load straight from global
+// memory into registers: the direct load is faster for every 32-bit pass and
+// for 64-bit row passes (measured); 64-bit column passes keep the prefetch.
 template <typename W, bool ROW>
 struct Prefetch {
     static constexpr bool ON = !ROW && sizeof(W) == 8;
@@ -796,7 +797,8 @@ __device__ __forceinline__ void pass_loop_tma(const PassArgs<W> &a, const CUtens
     }
 }
 
-// One pass over a batch: persistent CTAs with cp.async double buffering.
+// One pass over a batch: persistent CTAs; prefetching passes double-buffer
+// their tiles with cp.async, the others use one buffer and load directly.
 template <typename W, int DIR, int VAR, int LOGR, bool ROW, int TVC>
 __device__ __forceinline__ void pass_loop(const PassArgs<W> &a, uint4 *sm) {
     const Geo<W, LOGR, ROW, TVC> geo(a);
