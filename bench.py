@@ -434,7 +434,7 @@ def run_uneven(args, dist, rank, world):
     build.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     spec = uneven_batch_spec()
-    plans, descs, bfly, nbytes = {}, [], 0, 0
+    plans, descs, bfly, nbytes, pass_bytes = {}, [], 0, 0, 0
     for d in spec:
         L = 1 << d["logL"]
         key = (d["p"], L)
@@ -445,6 +445,7 @@ def run_uneven(args, dist, rank, world):
         descs.append((plans[key], t, d["inverse"]))
         bfly += d["logL"] * L // 2
         nbytes += 8 * L
+        pass_bytes += 8 * L * plans[key].info().n_passes
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
@@ -486,7 +487,9 @@ def run_uneven(args, dist, rank, world):
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
         "hbm_gbs_useful": gbs,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_uneven (one launch per step)"},
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "k_uneven (one launch per step)",
+                     "per_pass": {"achieved": pass_bytes / per / 1e9, "frac": pass_bytes / per / 1e9 / peaks["hbm_gbs"],
+                                  "note": "every word read and written once per pass (two passes above 2^11)"}},
         "gpu_launches": 1, "graph": "one CUDA graph replay per step", "clocks": clocks,
     }
 
