@@ -36,3 +36,17 @@ def test_library_exports_declared_symbols():
 def test_binding_covers_declared_symbols():
     names = set(declared_functions())
     assert names <= set(ntt._lib.exported_symbols()), names - set(ntt._lib.exported_symbols())
+
+
+def test_wait_hooks_validate_arguments_without_a_gpu():
+    """The failure-detection hooks are host-only setters: they validate their
+    arguments and need no device (the GPU tests use them to make a wait run out)."""
+    b.build()
+    lib = ntt._lib.load()
+    assert lib.ntt_pass_set_wait_budget(0, 0) == -4          # budget must be positive
+    assert lib.ntt_pass_set_wait_budget(1000, 8) == -4       # stall bytes: multiples of 16
+    assert lib.ntt_pass_set_wait_budget(1000, 1 << 17) == -4  # at most 65536
+    assert lib.ntt_pass_set_wait_budget(1000, 16) == 0
+    assert lib.ntt_pass_set_wait_budget(2_000_000_000, 0) == 0  # back to normal waits
+    assert lib.ntt_uneven_set_wait_budget(0, -1) == -4
+    assert lib.ntt_uneven_set_wait_budget(2_000_000_000, -1) == 0
