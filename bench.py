@@ -823,6 +823,9 @@ def run_ours(args, dist, rank, world):
     return line
 
 
+REF_STEP_BUDGET_S = 6.0  # upper bound on one reference step's oracle time (seconds)
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores, same config, metric and unit.
     Each step is a bounded sample of the workload (whole transforms)."""
@@ -832,7 +835,7 @@ def run_reference(args, rank, world):
     if args.workload in ("c4", "c5"):
         return run_reference_sampled(args, world)
     groups = spec["groups"]
-    budget = max(0.5, min(6.0, 60.0 / max(args.steps + args.warmup, 1)))
+    budget = min(REF_STEP_BUDGET_S, max(0.5, min(6.0, 60.0 / max(args.steps + args.warmup, 1))))
     for _ in range(args.warmup):
         cpu_sample(groups, budget)
     bf_total, t_total, desc = 0, 0.0, ""
