@@ -141,6 +141,9 @@ int ntt_plan_autotune(ntt_plan_t plan, size_t batch, int use_cache, int *log_r_o
  * [0, 2p) for the lazy variant (Algorithm 3's input range) and must lie in
  * [0, p) for NTT_VARIANT_NTL; the output is in [0, p), bit-reversed order.
  * stride_words >= L and stride_words*word_bytes a multiple of 16.
+ * 64-bit column passes fetch their tiles by tensor copies whose waits are
+ * bounded: a copy that never lands ends the pass early with NTT_ERR_TIMEOUT
+ * in the device status word (ntt_pass_status), never a hang.
  * Errors: NTT_ERR_ARG, NTT_ERR_ALIGN, NTT_ERR_CUDA (launch failure). */
 int ntt_forward_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride_words, void *stream);
 
