@@ -57,6 +57,7 @@ extern "C" {
 #define NTT_ERR_CANCELLED -11 /* server: request was cancelled */
 #define NTT_ERR_PENDING -12  /* server: request not finished yet */
 #define NTT_ERR_FAILED -13   /* server: request failed */
+#define NTT_ERR_INPUT -14    /* checked mode: an input residue lies outside the accepted range */
 
 /* Butterfly variants (ntt_plan_set_variant). */
 #define NTT_VARIANT_LAZY 0 /* Algorithms 3 (forward) and 4 (inverse), redundant residues */
@@ -153,6 +154,25 @@ int ntt_forward_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride
  * [0, p), UNNORMALISED: inverse(forward(a)) = L * a.  Layout and errors as
  * ntt_forward_batch. */
 int ntt_inverse_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride_words, void *stream);
+
+/* Input-range check (the checked mode of the library; Algorithms 3 and 4
+ * state their input intervals, and outside them the redundant-residue bounds
+ * of Theorems 2 and 3 do not hold).  Scans the `batch` vectors of L words at
+ * d_data (layout as ntt_forward_batch) for a word >= the bound the plan's
+ * variant accepts: 2p for a forward and 4p for an inverse transform with the
+ * lazy or Montgomery variant, p with NTT_VARIANT_NTL.  *first_bad receives
+ * the smallest flat index b*L + i of such a word, or -1.  Synchronous: runs
+ * one kernel on `stream` and waits for it.  Errors: NTT_ERR_ARG,
+ * NTT_ERR_ALIGN, NTT_ERR_RANGE, NTT_ERR_NOMEM, NTT_ERR_CUDA. */
+int ntt_check_input(ntt_plan_t plan, int inverse, const void *d_data, size_t batch, size_t stride_words,
+                    void *stream, long long *first_bad);
+
+/* Checked mode on (on != 0) or off for a plan: ntt_forward_batch and
+ * ntt_inverse_batch then run ntt_check_input first (synchronously) and
+ * return NTT_ERR_INPUT, leaving the data untouched, when a word is out of
+ * range.  Off by default: the unchecked calls are asynchronous and leave
+ * out-of-range inputs undefined.  Errors: NTT_ERR_ARG. */
+int ntt_plan_set_checked(ntt_plan_t plan, int on);
 
 /* One execution step (one pass, one kernel launch) of a transform: steps
  * 0 .. n_passes-1 run in order are exactly ntt_forward_batch (inverse = 0) or

@@ -84,6 +84,10 @@ class Plan:
     def set_variant(self, variant: int) -> None:
         check(_lib.load().ntt_plan_set_variant(self.handle, variant), "ntt_plan_set_variant")
 
+    def set_checked(self, on: bool) -> None:
+        """Checked mode: transforms validate their input range first (NTT_ERR_INPUT)."""
+        check(_lib.load().ntt_plan_set_checked(self.handle, 1 if on else 0), "ntt_plan_set_checked")
+
     def set_split(self, log_r) -> None:
         arr = (ctypes.c_int * len(log_r))(*log_r)
         check(_lib.load().ntt_plan_set_split(self.handle, len(log_r), arr), "ntt_plan_set_split")
@@ -121,6 +125,16 @@ def ntt_inverse_batch(plan: Plan, data, batch: int, stride_words: int | None = N
     stride = plan.L if stride_words is None else stride_words
     check(_lib.load().ntt_inverse_batch(plan.handle, _ptr(data), batch, stride, _stream(stream)),
           "ntt_inverse_batch")
+
+
+def ntt_check_input(plan: Plan, inverse: bool, data, batch: int, stride_words: int | None = None,
+                    stream=None) -> int:
+    """First flat index of an input word outside the accepted range, or -1 (synchronous)."""
+    stride = plan.L if stride_words is None else stride_words
+    bad = ctypes.c_longlong()
+    check(_lib.load().ntt_check_input(plan.handle, int(bool(inverse)), _ptr(data), batch, stride, _stream(stream),
+                                      ctypes.byref(bad)), "ntt_check_input")
+    return bad.value
 
 
 def ntt_execute_step(plan: Plan, inverse: bool, step: int, data, batch: int, stride_words: int | None = None,

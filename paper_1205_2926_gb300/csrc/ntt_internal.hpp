@@ -62,6 +62,8 @@ struct ntt_plan_s {
     cudaStream_t hs_in = nullptr, hs_out = nullptr;
     cudaEvent_t hev_start = nullptr, hev_end = nullptr;
     cudaEvent_t hev_in[16] = {}, hev_done[16] = {};
+    bool checked = false;        // checked mode: validate input ranges before each transform
+    void *check_word = nullptr;  // device word of ntt_check_input (allocated on first use)
     std::mutex mu;
 };
 

@@ -316,6 +316,16 @@ static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
 
 // ---------------------------------------------------------------- launches
 
+// Input-range check (checked mode): the smallest flat index b*L + i whose
+// word is >= bound, by an atomic minimum over a grid-stride scan.
+template <typename W>
+__global__ void k_check_input(const W *__restrict__ d, uint64_t stride, int logL, uint64_t total, W bound,
+                              unsigned long long *first) {
+    const uint64_t mask = (1ull << logL) - 1;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x)
+        if (d[(i >> logL) * stride + (i & mask)] >= bound) atomicMin(first, (unsigned long long)i);
+}
+
 // Wait budget of the pass kernels' tile copies and the test hook of
 // ntt_pass_set_wait_budget.
 static std::atomic<long long> g_pass_budget{2000000000LL};
@@ -513,6 +523,7 @@ const char *ntt_strerror(int code) {
         case NTT_ERR_CANCELLED: return "request cancelled";
         case NTT_ERR_PENDING: return "request pending";
         case NTT_ERR_FAILED: return "request failed";
+        case NTT_ERR_INPUT: return "input residue outside the accepted range";
         default: return "unknown status";
     }
 }
@@ -588,6 +599,7 @@ int ntt_plan_destroy(ntt_plan_t pl) {
     cudaDeviceSynchronize();
     free_tables(pl);
     release_host_pipeline(pl);
+    if (pl->check_word) cudaFree(pl->check_word);
     delete pl;
     return NTT_OK;
 }
@@ -636,14 +648,68 @@ static int check_batch_args(ntt_plan_t pl, const void *d, size_t batch, size_t s
     return NTT_OK;
 }
 
+int ntt_check_input(ntt_plan_t pl, int inverse, const void *d_data, size_t batch, size_t stride_words, void *stream,
+                    long long *first_bad) {
+    int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc) return rc;
+    if ((inverse != 0 && inverse != 1) || !first_bad) return NTT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(pl->mu);
+    cudaError_t e = cudaSuccess;
+    if (!pl->check_word) {
+        e = cudaMalloc(&pl->check_word, sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            pl->check_word = nullptr;
+            return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "check word");
+        }
+    }
+    unsigned long long *word = static_cast<unsigned long long *>(pl->check_word);
+    const uint64_t bound = pl->variant == NTT_VARIANT_NTL ? pl->p : (inverse ? 4 : 2) * pl->p;
+    const uint64_t total = (uint64_t)batch * pl->L;
+    const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 152 * 8);
+    e = cudaMemsetAsync(word, 0xff, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "check memset");
+    if (pl->wbytes == 4)
+        k_check_input<uint32_t><<<grid, 256, 0, st>>>(static_cast<const uint32_t *>(d_data), stride_words, pl->logL,
+                                                      total, (uint32_t)bound, word);
+    else
+        k_check_input<uint64_t><<<grid, 256, 0, st>>>(static_cast<const uint64_t *>(d_data), stride_words, pl->logL,
+                                                      total, bound, word);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "check launch");
+    unsigned long long h = ~0ull;
+    e = cudaMemcpyAsync(&h, word, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "check result");
+    *first_bad = h == ~0ull ? -1 : (long long)h;
+    return NTT_OK;
+}
+
+int ntt_plan_set_checked(ntt_plan_t pl, int on) {
+    if (!pl) return NTT_ERR_ARG;
+    pl->checked = on != 0;
+    return NTT_OK;
+}
+
+// Checked mode: the input-range check before a transform.
+static int checked_gate(ntt_plan_t pl, int inverse, const void *d, size_t batch, size_t stride, void *stream) {
+    if (!pl->checked) return NTT_OK;
+    long long bad = -1;
+    int rc = ntt_check_input(pl, inverse, d, batch, stride, stream, &bad);
+    if (rc) return rc;
+    return bad < 0 ? NTT_OK : NTT_ERR_INPUT;
+}
+
 int ntt_forward_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_words, void *stream) {
     int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc == NTT_OK) rc = checked_gate(pl, 0, d_data, batch, stride_words, stream);
     if (rc) return rc;
     return enqueue_transform(pl, 0, d_data, batch, stride_words, (cudaStream_t)stream);
 }
 
 int ntt_inverse_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_words, void *stream) {
     int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc == NTT_OK) rc = checked_gate(pl, 1, d_data, batch, stride_words, stream);
     if (rc) return rc;
     return enqueue_transform(pl, 1, d_data, batch, stride_words, (cudaStream_t)stream);
 }

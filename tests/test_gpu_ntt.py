@@ -351,3 +351,51 @@ def test_tile_copy_wait_times_out_and_recovers():
         ntt.ntt_pass_set_wait_budget(0, 0)
     assert e.value.code == -4
     plan.destroy()
+
+
+@pytest.mark.parametrize("p", [P_NTT30, P_NTT62])
+def test_checked_mode_input_ranges(p):
+    """Checked mode: the input-range check finds the first word outside the
+    interval the variant accepts (Algorithm 3: [0, 2p), Algorithm 4: [0, 4p),
+    Algorithm 2: [0, p)), and a checked transform refuses such a batch with
+    NTT_ERR_INPUT and leaves it untouched; in-range batches transform exactly."""
+    torch = require_gpu()
+    o = orc()
+    L, batch = 1 << 12, 3
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    dt = word_dtype(p)
+    a = batch_inputs(950, batch, L, p)
+    stride = pad_stride(L, plan.word_bytes, 3)
+    buf = np.zeros((batch, stride), dtype=dt)
+    buf[:, :L] = a
+    buf[:, L:] = np.iinfo(dt).max  # padding is outside the transforms and never checked
+    d = to_dev(buf, torch)
+    assert ntt.ntt_check_input(plan, False, d, batch, stride) == -1
+    # a word in [2p, 4p): out of range forward, in range inverse (lazy), out of range for NTL
+    bad = buf.copy()
+    bad[1, 777] = dt(3 * p)
+    bad[2, 5] = dt(2 * p)
+    db = to_dev(bad, torch)
+    assert ntt.ntt_check_input(plan, False, db, batch, stride) == 1 * L + 777
+    assert ntt.ntt_check_input(plan, True, db, batch, stride) == -1
+    plan.set_variant(1)
+    assert ntt.ntt_check_input(plan, True, db, batch, stride) == 1 * L + 777
+    assert ntt.ntt_check_input(plan, False, d, batch, stride) == -1
+    plan.set_variant(0)
+    bad[0, 9] = dt(4 * p)
+    db = to_dev(bad, torch)
+    assert ntt.ntt_check_input(plan, True, db, batch, stride) == 9
+    # checked transforms
+    plan.set_checked(True)
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_forward_batch(plan, db, batch, stride)
+    assert e.value.code == -14
+    torch.cuda.synchronize()
+    assert np.array_equal(from_dev(db, dt).reshape(batch, stride), bad), "a refused batch was modified"
+    ntt.ntt_forward_batch(plan, d, batch, stride)
+    torch.cuda.synchronize()
+    got = from_dev(d, dt).reshape(batch, stride)[:, :L]
+    assert np.array_equal(got.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64)))
+    plan.set_checked(False)
+    plan.destroy()
