@@ -399,3 +399,46 @@ def test_checked_mode_input_ranges(p):
     assert np.array_equal(got.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64)))
     plan.set_checked(False)
     plan.destroy()
+
+
+def _times_pow2_mod(x: np.ndarray, k: int, p: int) -> np.ndarray:
+    """x * 2^k mod p for residues x < p < 2^62, by k modular doublings (exact in uint64)."""
+    x = x.astype(np.uint64).copy()
+    pp = np.uint64(p)
+    for _ in range(k):
+        x = x + x
+        x = np.where(x >= pp, x - pp, x)
+    return x
+
+
+def test_largest_transforms():
+    """Maximum sizes: the 32-bit prime's largest length 2^23 against the oracle
+    element by element, and the plans' largest length 2^26 (64-bit words, the
+    smallest prime above 2^61 that is 1 mod 2^26) on sampled outputs of the
+    definition plus inverse(forward(a)) = L a on every element."""
+    torch = require_gpu()
+    o = orc()
+    # 2^23, 32-bit words: the whole transform both ways
+    p, L = P_NTT30, 1 << 23
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L)
+    a = batch_inputs(960, 1, L, p)
+    fwd = run(plan, a, False, None, 0, torch)
+    assert np.array_equal(fwd.astype(np.uint64), o.ntt_ref(p, w, a.astype(np.uint64)))
+    back = run(plan, fwd, True, None, 0, torch)
+    assert np.array_equal(back[0].astype(np.uint64), _times_pow2_mod(a[0], 23, p))
+    plan.destroy()
+    # 2^26, 64-bit words
+    q = o.find_prime_above(1 << 61, 26)
+    assert q == ntt.find_prime(1 << 61, 26) and o.is_prime(q) and (q - 1) % (1 << 26) == 0
+    L = 1 << 26
+    w = o.root_of_unity(q, L)
+    plan = ntt.ntt_plan(q, w, L)
+    a = batch_inputs(961, 1, L, q)
+    fwd = run(plan, a, False, None, 0, torch)
+    rng = np.random.default_rng(5)
+    for k in [0, 1, L - 1, L // 2] + [int(x) for x in rng.integers(0, L, size=4)]:
+        assert int(fwd[0, k]) == o.dft_at(q, w, a[0], k), f"output {k}"
+    back = run(plan, fwd, True, None, 0, torch)
+    assert np.array_equal(back[0].astype(np.uint64), _times_pow2_mod(a[0], 26, q))
+    plan.destroy()
