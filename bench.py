@@ -658,7 +658,7 @@ STEADY = {
 }
 
 
-def steady_state(cases, torch, ntt, peak_gbs, K=20):
+def steady_state(cases, torch, ntt, peak_gbs, K=20, warm=3):
     """The pass kernels at 256 MiB per pass (twice the L2, so every pass reads
     and writes HBM): per pass and per whole forward+inverse transform, useful
     bytes (one read and one write of every word per pass) over the CUDA-event
@@ -675,7 +675,7 @@ def steady_state(cases, torch, ntt, peak_gbs, K=20):
         passes, total_us = [], 0.0
         for inv in (0, 1):
             for k in range(len(split)):
-                for _ in range(3):
+                for _ in range(warm):
                     ntt.ntt_execute_step(plan, inv, k, t, b)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
@@ -698,6 +698,23 @@ def steady_state(cases, torch, ntt, peak_gbs, K=20):
         plan.destroy()
     torch.cuda.synchronize()
     return out
+
+
+def run_steady_only(args):
+    """Only the 256 MiB per-pass report of the workload's lengths: with
+    --steady-launches 1 every pass of every case launches exactly once, in
+    order (forward passes, then inverse passes), so that a profiler can
+    capture them by position."""
+    import torch
+    import paper_1205_2926_gb300 as ntt
+    from paper_1205_2926_gb300 import build
+    build.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    K = max(1, args.steady_launches)
+    cases = STEADY.get(args.workload, STEADY["c2"])
+    return {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
+            "launches_per_pass": K,
+            "cases": steady_state(cases, torch, ntt, load_peaks()["hbm_gbs"], K=K, warm=3 if K > 1 else 0)}
 
 
 def run_ours(args, dist, rank, world):
@@ -812,7 +829,8 @@ def run_ours(args, dist, rank, world):
     if args.workload in STEADY and not args.no_steady_state:
         try:
             line["steady_state"] = {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
-                                    "cases": steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"])}
+                                    "cases": steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"],
+                                                          K=max(1, args.steady_launches))}
         except Exception as e:  # a report of its own; the headline above stands
             line["steady_state"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_serving and args.workload == "c2":
@@ -925,6 +943,10 @@ def main():
                     help="serving run length (default: 60 s for --workload c5, 2 s inside the default bench)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-steady-state", action="store_true", help="skip the 256 MiB per-pass report")
+    ap.add_argument("--steady-only", action="store_true",
+                    help="only the 256 MiB per-pass report (for profiling the pass kernels at that size)")
+    ap.add_argument("--steady-launches", type=int, default=20,
+                    help="timed launches per pass in the 256 MiB report (1: no warm-up, one launch per pass)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -958,7 +980,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    if args.workload == "probe":
+    if args.steady_only:
+        line = run_steady_only(args)
+    elif args.workload == "probe":
         line = run_probe()
     elif args.workload == "c4":
         line = run_uneven(args, dist, rank, world)
