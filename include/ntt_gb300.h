@@ -174,6 +174,25 @@ int ntt_check_input(ntt_plan_t plan, int inverse, const void *d_data, size_t bat
  * out-of-range inputs undefined.  Errors: NTT_ERR_ARG. */
 int ntt_plan_set_checked(ntt_plan_t plan, int on);
 
+/* Forward transform from bit-reversed input to natural-order output: the
+ * schedule of ntt_inverse_batch (Algorithm 1 run backwards, Section 4, with
+ * the Algorithm 4 butterfly) driven by the forward root's tables, so
+ * out[i] = sum_j omega^(i j) x[rev(j)]: applied to the bit-reversal of a, the
+ * DFT of a in natural order.  The pair ntt_inverse_dif_batch /
+ * ntt_forward_dit_batch mirrors ntt_forward_batch / ntt_inverse_batch with
+ * the roots exchanged.  Input residues in [0, 4p) (lazy, Montgomery) or [0, p) (NTL);
+ * output in [0, p).  Layout and errors as ntt_forward_batch (plus
+ * NTT_ERR_INPUT in checked mode). */
+int ntt_forward_dit_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride_words, void *stream);
+
+/* Inverse transform from natural-order input to bit-reversed output: the
+ * schedule of ntt_forward_batch (Algorithm 1, Algorithm 3 butterflies) driven
+ * by the inverse root's tables, so position k holds
+ * sum_i omega^(-i rev(k)) x[i] (unnormalised).  Input residues in [0, 2p)
+ * (lazy, Montgomery) or [0, p) (NTL); output in [0, p).  Layout and errors
+ * as ntt_forward_batch. */
+int ntt_inverse_dif_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride_words, void *stream);
+
 /* One execution step (one pass, one kernel launch) of a transform: steps
  * 0 .. n_passes-1 run in order are exactly ntt_forward_batch (inverse = 0) or
  * ntt_inverse_batch (inverse = 1); intermediate contents between steps are

@@ -127,6 +127,20 @@ def ntt_inverse_batch(plan: Plan, data, batch: int, stride_words: int | None = N
           "ntt_inverse_batch")
 
 
+def ntt_forward_dit_batch(plan: Plan, data, batch: int, stride_words: int | None = None, stream=None) -> None:
+    """Forward transform, bit-reversed input to natural-order output."""
+    stride = plan.L if stride_words is None else stride_words
+    check(_lib.load().ntt_forward_dit_batch(plan.handle, _ptr(data), batch, stride, _stream(stream)),
+          "ntt_forward_dit_batch")
+
+
+def ntt_inverse_dif_batch(plan: Plan, data, batch: int, stride_words: int | None = None, stream=None) -> None:
+    """Inverse transform (unnormalised), natural-order input to bit-reversed output."""
+    stride = plan.L if stride_words is None else stride_words
+    check(_lib.load().ntt_inverse_dif_batch(plan.handle, _ptr(data), batch, stride, _stream(stream)),
+          "ntt_inverse_dif_batch")
+
+
 def ntt_check_input(plan: Plan, inverse: bool, data, batch: int, stride_words: int | None = None,
                     stream=None) -> int:
     """First flat index of an input word outside the accepted range, or -1 (synchronous)."""

@@ -63,6 +63,8 @@ _SIGNATURES = {
     "ntt_plan_set_split": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int)]),
     "ntt_plan_autotune": (c_int, [c_void_p, c_size, c_int, ctypes.POINTER(c_int)]),
     "ntt_forward_batch": (c_int, [c_void_p, c_void_p, c_size, c_size, c_void_p]),
+    "ntt_forward_dit_batch": (c_int, [c_void_p, c_void_p, c_size, c_size, c_void_p]),
+    "ntt_inverse_dif_batch": (c_int, [c_void_p, c_void_p, c_size, c_size, c_void_p]),
     "ntt_inverse_batch": (c_int, [c_void_p, c_void_p, c_size, c_size, c_void_p]),
     "ntt_execute_step": (c_int, [c_void_p, c_int, c_int, c_void_p, c_size, c_size, c_void_p]),
     "ntt_transform_host": (c_int, [c_void_p, c_int, c_void_p, c_size, c_size, c_void_p]),

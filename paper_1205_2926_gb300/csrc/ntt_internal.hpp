@@ -106,6 +106,13 @@ int enqueue_transform(ntt_plan_s *plan, int dir, void *data, size_t batch, size_
 
 // Enqueue execution steps first .. first+count-1 of a transform (a step is
 // one pass; the inverse executes the passes in reverse order).
+// The same with the twiddle tables of root direction `roots` (0: omega,
+// 1: omega^-1) in the schedule of direction `dir`: dir = 1, roots = 0 is the
+// forward transform from bit-reversed to natural order (DIT), dir = 0,
+// roots = 1 the inverse from natural to bit-reversed order (DIF).
+int enqueue_steps_roots(ntt_plan_s *plan, int dir, int roots, void *data, size_t batch, size_t stride,
+                        cudaStream_t st, int first, int count);
+
 int enqueue_steps(ntt_plan_s *plan, int dir, void *data, size_t batch, size_t stride, cudaStream_t st, int first,
                   int count);
 

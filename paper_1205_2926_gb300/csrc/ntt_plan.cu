@@ -396,6 +396,11 @@ int enqueue_transform(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t 
 
 int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stride, cudaStream_t st, int first,
                   int count) {
+    return enqueue_steps_roots(pl, dir, dir, data, batch, stride, st, first, count);
+}
+
+int enqueue_steps_roots(ntt_plan_s *pl, int dir, int roots, void *data, size_t batch, size_t stride,
+                        cudaStream_t st, int first, int count) {
     LaunchSpec s;
     memset(&s, 0, sizeof(s));
     s.data = data;
@@ -407,7 +412,7 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
     s.wait_budget = g_pass_budget.load();
     s.tx_extra = g_pass_extra.load();
     const bool mont = pl->variant == NTT_VARIANT_MONT;
-    s.tw = mont ? pl->twm[dir] : pl->tw[dir];
+    s.tw = mont ? pl->twm[roots] : pl->tw[roots];
     if (pl->logL <= 2) {
         s.grid = (unsigned)((batch + 127) / 128);
         cudaError_t e = launch(pl, s, 2, dir, st);
@@ -425,8 +430,8 @@ int enqueue_steps(ntt_plan_s *pl, int dir, void *data, size_t batch, size_t stri
         if (kind == 0) {
             s.logTA = ps.logTA;
             s.flags |= 2 | (ps.has_mb ? 4 : 0);  // F_MIDDLE, F_MB
-            s.ma = mont ? ps.mam[dir] : ps.ma[dir];
-            s.mb = mont ? ps.mbm[dir] : ps.mb[dir];
+            s.ma = mont ? ps.mam[roots] : ps.ma[roots];
+            s.mb = mont ? ps.mbm[roots] : ps.mb[roots];
         } else {
             s.ma = s.mb = nullptr;
         }
@@ -712,6 +717,22 @@ int ntt_inverse_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_w
     if (rc == NTT_OK) rc = checked_gate(pl, 1, d_data, batch, stride_words, stream);
     if (rc) return rc;
     return enqueue_transform(pl, 1, d_data, batch, stride_words, (cudaStream_t)stream);
+}
+
+int ntt_forward_dit_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_words, void *stream) {
+    int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc == NTT_OK) rc = checked_gate(pl, 1, d_data, batch, stride_words, stream);  // Algorithm 4's input range
+    if (rc) return rc;
+    return enqueue_steps_roots(pl, 1, 0, d_data, batch, stride_words, (cudaStream_t)stream, 0,
+                               pl->logL <= 2 ? 1 : pl->npass);
+}
+
+int ntt_inverse_dif_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_words, void *stream) {
+    int rc = check_batch_args(pl, d_data, batch, stride_words);
+    if (rc == NTT_OK) rc = checked_gate(pl, 0, d_data, batch, stride_words, stream);  // Algorithm 3's input range
+    if (rc) return rc;
+    return enqueue_steps_roots(pl, 0, 1, d_data, batch, stride_words, (cudaStream_t)stream, 0,
+                               pl->logL <= 2 ? 1 : pl->npass);
 }
 
 int ntt_execute_step(ntt_plan_t pl, int inverse, int step, void *d_data, size_t batch, size_t stride_words,

@@ -442,3 +442,41 @@ def test_largest_transforms():
     back = run(plan, fwd, True, None, 0, torch)
     assert np.array_equal(back[0].astype(np.uint64), _times_pow2_mod(a[0], 26, q))
     plan.destroy()
+
+
+@pytest.mark.parametrize("p", [P_NTT30, P_NTT62])
+@pytest.mark.parametrize("logL", [2, 3, 10, 16, 20])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_dit_forward_and_dif_inverse(p, logL, variant):
+    """The schedules with the roots exchanged: the forward transform from
+    bit-reversed to natural order is the oracle's backwards Algorithm 1 with
+    root omega^-1 inverted, i.e. sum_j omega^(ij) x[rev j]; the inverse from
+    natural to bit-reversed order is Algorithm 1 with root omega^-1."""
+    torch = require_gpu()
+    o = orc()
+    L, batch = 1 << logL, 2
+    w = o.root_of_unity(p, L)
+    wi = o.invmod(w, p)
+    plan = ntt.ntt_plan(p, w, L)
+    plan.set_variant(variant)
+    dt = word_dtype(p)
+    x = batch_inputs(970 + logL, batch, L, p)
+    d = to_dev(x, torch)
+    ntt.ntt_forward_dit_batch(plan, d, batch)
+    torch.cuda.synchronize()
+    got = from_dev(d, dt).reshape(batch, L).astype(np.uint64)
+    assert np.array_equal(got, o.intt_ref(p, wi, x.astype(np.uint64))), "DIT forward"
+    # applied to the bit-reversal of a: the DFT of a in natural order
+    rev = np.array([o.bitrev(k, logL) for k in range(L)]) if logL <= 10 else None
+    if rev is not None:
+        nat = o.ntt_ref(p, w, x.astype(np.uint64))[:, rev]  # undo the bit-reversed placement
+        d = to_dev(x[:, rev].copy(), torch)
+        ntt.ntt_forward_dit_batch(plan, d, batch)
+        torch.cuda.synchronize()
+        assert np.array_equal(from_dev(d, dt).reshape(batch, L).astype(np.uint64), nat)
+    d = to_dev(x, torch)
+    ntt.ntt_inverse_dif_batch(plan, d, batch)
+    torch.cuda.synchronize()
+    got = from_dev(d, dt).reshape(batch, L).astype(np.uint64)
+    assert np.array_equal(got, o.ntt_ref(p, wi, x.astype(np.uint64))), "DIF inverse"
+    plan.destroy()
