@@ -193,6 +193,19 @@ int ntt_forward_dit_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t st
  * as ntt_forward_batch. */
 int ntt_inverse_dif_batch(ntt_plan_t plan, void *d_data, size_t batch, size_t stride_words, void *stream);
 
+/* Host-only self-test of the launch geometry (no device needed): for every
+ * pass split that ntt_plan_set_split accepts, for every length 2^3..2^26, both
+ * word sizes and batches of 1 .. 16384 vectors (within the batch limit of the
+ * transform calls), checks that the tiles of each pass cover its data
+ * exactly once, that each sub-tile's threads form the contiguous block the
+ * kernels synchronise, that the shared-memory buffers match the kernels'
+ * compile-time layout (padded or not) and fit in 227 KiB, and that 64-bit
+ * tensor-copy boxes are well formed.  *n_checked receives the number of
+ * (split, pass, batch) cases; on the first violation returns NTT_ERR_RANGE
+ * with a description in msg (msg_len bytes, may be NULL).  Returns NTT_OK or
+ * NTT_ERR_ARG. */
+int ntt_selftest_geometry(long long *n_checked, char *msg, int msg_len);
+
 /* One execution step (one pass, one kernel launch) of a transform: steps
  * 0 .. n_passes-1 run in order are exactly ntt_forward_batch (inverse = 0) or
  * ntt_inverse_batch (inverse = 1); intermediate contents between steps are

@@ -2,6 +2,7 @@
 // device tables, the pass schedule, and the transform entry points of the C ABI.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -290,7 +291,9 @@ static int build_tables(ntt_plan_s *pl) {
     return rc;
 }
 
-static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
+// Pass geometry of a split (no device work): radix, stride, tile width and
+// middle-table shape of every pass.
+static void set_geometry(ntt_plan_s *pl, int n, const int *logr) {
     pl->npass = n;
     const int logV = pl->wbytes == 4 ? 2 : 1;
     int logB = pl->logL;
@@ -311,6 +314,10 @@ static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
         }
         logB -= logr[q];
     }
+}
+
+static int apply_split(ntt_plan_s *pl, int n, const int *logr) {
+    set_geometry(pl, n, logr);
     return build_tables(pl);
 }
 
@@ -484,6 +491,68 @@ void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s, boo
         s.buf_chunks = ((uint32_t)s.per_cta * nsp) << logTV;
         s.nrows = 0;
     }
+}
+
+// Host-only self-test of the launch geometry against the kernels' compile-time
+// layout, for every allowed split of every length 2^3..2^26, both word sizes
+// and a range of batch sizes (see the header).
+template <typename W, int LOGR>
+static int tvf_t() {
+    return ColWidth<LOGR, ColTileLog<W, LOGR>::MAX>::LOGTV;
+}
+template <typename W>
+static int tvf(int logR) {
+    static const int t[12] = {0, 0, 0, tvf_t<W, 3>(), tvf_t<W, 4>(), tvf_t<W, 5>(), tvf_t<W, 6>(), tvf_t<W, 7>(),
+                              tvf_t<W, 8>(), tvf_t<W, 9>(), tvf_t<W, 10>(), tvf_t<W, 11>()};
+    return t[logR];
+}
+
+static bool geometry_ok(const ntt_plan_s &pl, int q, uint64_t batch, bool persistent, char *msg, int msg_len) {
+    LaunchSpec s;
+    memset(&s, 0, sizeof(s));
+    tile_params(&pl, q, batch, s, persistent);
+    const PassPlan &ps = pl.pass[q];
+    const int logV = pl.wbytes == 4 ? 2 : 1;
+    const uint64_t R = 1ull << ps.logR;
+    const bool row = q == pl.npass - 1;
+    const size_t smem_max = 232448;  // 227 KiB of shared memory per CTA
+    auto fail = [&](const char *what) {
+        if (msg && msg_len > 0)
+            snprintf(msg, msg_len, "w%d L=2^%d pass %d/%d log R=%d batch=%llu%s: %s", pl.wbytes * 8, pl.logL, q,
+                     pl.npass, ps.logR, (unsigned long long)batch, persistent ? " (uneven)" : "", what);
+        return false;
+    };
+    if (s.per_cta < 1 || s.ntiles < 1) return fail("empty tiling");
+    if (row) {
+        const uint64_t units = (uint64_t)s.per_cta * (R >> 3);
+        if (units != (uint64_t)kThreads) return fail("row tile is not one unit per thread");
+        const uint64_t nrows = batch << (pl.logL - ps.logR), per = (uint64_t)s.per_cta << logV;
+        if (s.nrows != nrows) return fail("row count");
+        if ((uint64_t)s.ntiles * per < nrows || (uint64_t)(s.ntiles - 1) * per >= nrows) return fail("row tiles");
+        if (s.buf_chunks != (uint32_t)s.per_cta * (R + R / 8)) return fail("row buffer");
+        if ((size_t)s.buf_chunks * 16 > smem_max) return fail("row buffer exceeds shared memory");
+        return true;
+    }
+    const int ltb = ps.logS - s.logTV - logV, lbt = pl.logL - ps.logR - ps.logS;
+    if (s.logTV < 0 || ltb < 0 || lbt < 0) return fail("column geometry");
+    const uint64_t sub = batch << (ltb + lbt);
+    if ((uint64_t)s.ntiles * s.per_cta < sub || (uint64_t)(s.ntiles - 1) * s.per_cta >= sub) return fail("column tiles");
+    const int logT = ps.logR - 3 + s.logTV;  // threads (units) of one sub-tile
+    const uint64_t units = (uint64_t)s.per_cta << logT;
+    if (logT < 8 ? units != (uint64_t)kThreads : units % kThreads != 0)
+        return fail("sub-tiles are not contiguous thread blocks");
+    // the kernel's shared layout: unpadded exactly when its compile-time width is 8 vectors
+    const int tv_kernel = pl.wbytes == 4 ? tvf<uint32_t>(ps.logR) : tvf<uint64_t>(ps.logR);
+    if (!persistent && s.logTV > tv_kernel) return fail("tile wider than the kernel's widest");
+    const bool dense = s.logTV == 3;
+    if (dense && tv_kernel != 3) return fail("unpadded tile for a padded kernel layout");
+    const uint64_t nsp = dense ? R : R + R / 8;
+    if (s.buf_chunks != ((uint32_t)s.per_cta * nsp << s.logTV)) return fail("column buffer");
+    const bool two = pl.wbytes == 8;  // prefetching passes hold two buffers (tensor copies add two mbarriers)
+    if ((size_t)(two ? 2 : 1) * s.buf_chunks * 16 + 16 > smem_max) return fail("column buffers exceed shared memory");
+    if (two && dense && (((uint64_t)pl.wbytes << ps.logS) < 128 || (R > 256 && R % 256)))
+        return fail("tensor-copy box");
+    return true;
 }
 
 }  // namespace ntt
@@ -717,6 +786,44 @@ int ntt_inverse_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_w
     if (rc == NTT_OK) rc = checked_gate(pl, 1, d_data, batch, stride_words, stream);
     if (rc) return rc;
     return enqueue_transform(pl, 1, d_data, batch, stride_words, (cudaStream_t)stream);
+}
+
+int ntt_selftest_geometry(long long *n_checked, char *msg, int msg_len) {
+    if (!n_checked) return NTT_ERR_ARG;
+    *n_checked = 0;
+    if (msg && msg_len > 0) msg[0] = 0;
+    for (int wb : {4, 8}) {
+        for (int logL = 3; logL <= 26; ++logL) {
+            std::vector<std::vector<int>> splits;
+            for (int a = 3; a <= 11; ++a) {
+                splits.push_back({a, logL - a});
+                for (int b = 3; b <= 11; ++b) {
+                    splits.push_back({a, b, logL - a - b});
+                    for (int c = 3; c <= 11; ++c) splits.push_back({a, b, c, logL - a - b - c});
+                }
+            }
+            splits.push_back({logL});
+            for (const auto &sp : splits) {
+                if (!split_allowed(logL, wb, (int)sp.size(), sp.data())) continue;
+                ntt_plan_s pl;
+                pl.logL = logL;
+                pl.L = 1ull << logL;
+                pl.wbytes = wb;
+                set_geometry(&pl, (int)sp.size(), sp.data());
+                for (uint64_t batch : {1ull, 2ull, 3ull, 5ull, 64ull, 1000ull, 1ull << 14}) {
+                    if (batch > (1ull << 31) / std::max<uint64_t>(1, pl.L / 8)) continue;  // the API's batch limit
+                    for (int q = 0; q < pl.npass; ++q) {
+                        for (bool persistent : {false, true}) {
+                            if (persistent && (wb != 4 || logL > 16 || batch != 1)) continue;  // uneven batches
+                            ++*n_checked;
+                            if (!geometry_ok(pl, q, batch, persistent, msg, msg_len)) return NTT_ERR_RANGE;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    return NTT_OK;
 }
 
 int ntt_forward_dit_batch(ntt_plan_t pl, void *d_data, size_t batch, size_t stride_words, void *stream) {

@@ -50,3 +50,19 @@ def test_wait_hooks_validate_arguments_without_a_gpu():
     assert lib.ntt_pass_set_wait_budget(2_000_000_000, 0) == 0  # back to normal waits
     assert lib.ntt_uneven_set_wait_budget(0, -1) == -4
     assert lib.ntt_uneven_set_wait_budget(2_000_000_000, -1) == 0
+
+
+def test_launch_geometry_self_test_without_a_gpu():
+    """The library's host-side geometry self-test: every allowed split of every
+    length 2^3..2^26, both word sizes, batches 1..16384 -- tiles cover the data
+    exactly once, sub-tiles are contiguous thread blocks, shared buffers match
+    the kernels' layout and fit, tensor-copy boxes are well formed."""
+    import ctypes
+    b.build()
+    lib = ntt._lib.load()
+    n = ctypes.c_longlong()
+    msg = ctypes.create_string_buffer(256)
+    rc = lib.ntt_selftest_geometry(ctypes.byref(n), msg, 256)
+    assert rc == 0, msg.value.decode()
+    assert n.value > 10_000
+    assert lib.ntt_selftest_geometry(None, None, 0) == -4
