@@ -151,3 +151,18 @@ def test_bigint_oracle_closed_forms(n):
     x = np.arange(1, n + 1, dtype=np.uint32) * np.uint32(2654435761)
     assert list(map(int, oracle.bigint_mul(x, np.array([1], dtype=np.uint32)))) == list(map(int, x)) + [0]
     assert not oracle.bigint_mul(x, np.array([0], dtype=np.uint32)).any()
+
+
+def test_golden_file_regenerates_from_the_oracle(tmp_path):
+    """The stored forward golden file is exactly what its committed script
+    writes from the oracle (no value in it came from anywhere else)."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    out = tmp_path / "forward.txt"
+    mod.write_single_forward(str(out), P_NTT30, 1024, 1)
+    with open(os.path.join(here, "forward_p998244353_L1024_seed1.txt")) as f:
+        assert out.read_text() == f.read()
