@@ -230,11 +230,11 @@ void or_intt_ref(uint64_t p, uint64_t w, uint64_t L, uint64_t *x) {
 
 /* Batched forms: `batch` transforms at a distance of `stride` words. */
 void or_ntt_ref_batch(uint64_t p, uint64_t w, uint64_t L, uint64_t *x, uint64_t batch, uint64_t stride) {
-    for (uint64_t b = 0; b < batch; b++) or_ntt_ref(p, w, L, x + b * stride);
+    for (uint64_t b = 0; b < batch; b++) or_ntt_ref(p, w, L, x + b * (MUTANT(6) ? L : stride));
 }
 
 void or_intt_ref_batch(uint64_t p, uint64_t w, uint64_t L, uint64_t *x, uint64_t batch, uint64_t stride) {
-    for (uint64_t b = 0; b < batch; b++) or_intt_ref(p, w, L, x + b * stride);
+    for (uint64_t b = 0; b < batch; b++) or_intt_ref(p, w, L, x + b * (MUTANT(6) ? L : stride));
 }
 
 /* ------------------------------------------- polynomial multiplication */

@@ -195,3 +195,42 @@ def pin_dft_at(o):
 
 
 ALL_PINS.append(pin_dft_at)
+
+
+def pin_batch_wrappers(o):
+    """The batched forms (``batch`` transforms ``stride`` words apart, stride >
+    L) against Horner evaluation row by row, with the padding words between
+    rows left untouched.  Forward: position k of row b is row b's polynomial at
+    omega^rev(k) (Section 1 definition in Algorithm 1's order).  Inverse
+    (Section 4, unnormalised): position i is sum_j omega^(-i j) y[rev(j)], the
+    polynomial with coefficients y[rev(j)] evaluated at omega^-i."""
+    import ctypes
+    p64 = ctypes.POINTER(ctypes.c_uint64)
+    sentinel = np.uint64(0xA5A5A5A5A5A5A5A5)
+    for p in (17, 998244353, 2305843009448574977):
+        for l, batch, pad in ((2, 3, 1), (4, 5, 3), (6, 3, 7)):
+            L = 1 << l
+            if (p - 1) % L:
+                continue
+            w = primitive_root_of_order(p, L)
+            winv = pow(w, p - 2, p)
+            stride = L + pad
+            rows = [uniform_residues(8000 + 17 * l + b, L, p) for b in range(batch)]
+            for inverse in (False, True):
+                buf = np.full(batch * stride, sentinel, dtype=np.uint64)
+                for b in range(batch):
+                    buf[b * stride:b * stride + L] = rows[b]
+                fn = o.lib.or_intt_ref_batch if inverse else o.lib.or_ntt_ref_batch
+                fn(p, w, L, buf.ctypes.data_as(p64), batch, stride)
+                for b in range(batch):
+                    got = [int(v) for v in buf[b * stride:b * stride + L]]
+                    if inverse:
+                        coeffs = [int(rows[b][bitrev(j, l)]) for j in range(L)]
+                        want = [horner_eval(coeffs, pow(winv, i, p), p) for i in range(L)]
+                    else:
+                        want = [horner_eval(rows[b], pow(w, bitrev(k, l), p), p) for k in range(L)]
+                    assert got == want, (p, L, batch, stride, b, "inverse" if inverse else "forward")
+                    assert np.all(buf[b * stride + L:(b + 1) * stride] == sentinel), (p, L, b, "padding")
+
+
+ALL_PINS.append(pin_batch_wrappers)
