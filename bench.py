@@ -119,16 +119,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per launch of a pass kernel, from one ncu capture
-# of the current kernels (profiles/k_pass_u32_64x2p16_full.md), keyed by
-# workload and pass; passes without a capture report null.  The writes are 0:
-# the pass's output stays in the 129 MB L2 until it is evicted later.
-NCU_TRAFFIC = {
-    ("c2", "forward pass 0 of 64 x 2^16 (log2 R = 7)"): 17356800 + 0,
-    ("c2", "forward pass 1 of 64 x 2^16 (log2 R = 9)"): 16805376 + 0,
-    ("c2", "inverse pass 0 of 64 x 2^16 (log2 R = 9)"): 16810496 + 0,
-    ("c2", "inverse pass 1 of 64 x 2^16 (log2 R = 7)"): 17366784 + 0,
-}
+# DRAM bytes (read + write) per launch of the dominant pass kernel come from
+# one ncu capture summarised in profiles/dram_traffic.md: a table of
+# `| workload | kernel | bytes per launch | kernel source hash |` rows.  The
+# hash covers the pass kernels' sources; a row taken from other sources (the
+# kernels changed since the counters were taken) gives null, not a stale number.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+KERNEL_SOURCES = ["ntt_kernels.cuh", "modarith.cuh", "ntt_pass_inst.cuh", "ntt_pass_u32.cu", "ntt_pass_u64.cu",
+                  "ntt_plan.cu"]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1205_2926_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str, kernel: str):
+    """(bytes per launch or None, note) for a pass of a workload."""
+    try:
+        lines = open(TRAFFIC_PROFILE).read().splitlines()
+    except OSError:
+        return None, "no capture summarised"
+    want = kernel_source_hash()
+    for ln in lines:
+        f = [x.strip() for x in ln.strip().strip("|").split("|")]
+        if len(f) == 4 and f[0] == workload and f[1] == kernel:
+            if f[3] != want:
+                return None, f"capture of other kernel sources ({f[3]}; now {want})"
+            try:
+                return int(f[2]), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {os.path.basename(TRAFFIC_PROFILE)}"
+            except ValueError:
+                return None, "unreadable row"
+    return None, "kernel not captured"
 
 
 def alu_peak_bfly(word_bytes, sm_mhz):
@@ -639,13 +665,14 @@ def run_bigint(args, dist, rank, world):
 
 
 def run_probe():
-    """Build and run csrc/probe/butterfly_rate.cu: register-only butterfly and
-    multiply rates of this GPU (the integer-pipe roof of the NTT kernels)."""
+    """Build and run bench_probes/butterfly_rate.cu: register-only butterfly
+    and multiply rates of this GPU (the integer-pipe roof of the NTT kernels)."""
     from paper_1205_2926_gb300 import build as b
-    src = os.path.join(ROOT, "paper_1205_2926_gb300", "csrc", "probe", "butterfly_rate.cu")
-    exe = os.path.join(ROOT, "paper_1205_2926_gb300", "_build", "butterfly_rate")
+    src = os.path.join(ROOT, "bench_probes", "butterfly_rate.cu")
+    exe = os.path.join(ROOT, "bench_probes", "_build", "butterfly_rate")
     os.makedirs(os.path.dirname(exe), exist_ok=True)
-    subprocess.run([b._nvcc(), *b.ARCH, "-O3", "-std=c++17", src, "-o", exe], check=True)
+    subprocess.run([b._nvcc(), *b.ARCH, "-O3", "-std=c++17", "-I", os.path.join(ROOT, "paper_1205_2926_gb300", "csrc"),
+                    src, "-o", exe], check=True)
     r = subprocess.run([exe], capture_output=True, text=True, check=True)
     res = json.loads(r.stdout.strip().splitlines()[-1])
     return {"metric": "register-only butterflies per clock per SM", "value": res["lazy_fwd_bfly_per_clk_sm"],
@@ -658,12 +685,15 @@ STEADY = {
 }
 
 
-def steady_state(cases, torch, ntt, peak_gbs, K=20, warm=3):
-    """The pass kernels at 256 MiB per pass (twice the L2, so every pass reads
-    and writes HBM): per pass and per whole forward+inverse transform, useful
-    bytes (one read and one write of every word per pass) over the CUDA-event
-    time of K back-to-back launches, against the measured HBM copy peak.  The
-    split is the library's own for that batch (autotuned, cached)."""
+def steady_state(cases, torch, ntt, peak_gbs, K=20, warm=3, sm_mhz=2070.0):
+    """The pass kernels at 256 MiB per batch (twice the L2, so every pass reads
+    and writes HBM), CUDA-event time of K back-to-back launches of each pass.
+    Per pass: that pass's bytes (one read and one write of every word) over its
+    time.  Per transform: one read and one write of every word per direction
+    (the algorithmic bytes of the whole transform, however many passes it
+    takes) over the forward+inverse time, against the measured HBM copy peak;
+    and butterflies/s against the integer-multiply roof.  The split is the
+    library's own for that batch (autotuned, cached)."""
     out = []
     for p, l, b in cases:
         L = 1 << l
@@ -689,11 +719,16 @@ def steady_state(cases, torch, ntt, peak_gbs, K=20, warm=3):
                 passes.append({"pass": f"{'inverse' if inv else 'forward'} {k}",
                                "log2_R": (split[::-1] if inv else split)[k], "us": round(us, 1),
                                "GBs": round(gbs), "frac": round(gbs / peak_gbs, 3)})
-        moved = 2 * len(split) * 2 * b * L * w
+        # per transform (Section 5's unit of work): one read and one write of
+        # every word per direction, whatever the number of passes
+        per_transform = 2 * (2 * b * L * w)
+        bfly_s = 2 * b * (L // 2) * l / (total_us * 1e-6)
         out.append({"workload": f"{b} x 2^{l}, {8 * w}-bit words ({b * L * w >> 20} MiB)", "split": split,
                     "passes": passes, "fwd_inv_us": round(total_us, 1),
-                    "butterflies_per_s": 2 * b * (L // 2) * l / (total_us * 1e-6),
-                    "hbm_frac_of_transform": round(moved / (total_us * 1e-6) / 1e9 / peak_gbs, 3)})
+                    "butterflies_per_s": bfly_s,
+                    "hbm_frac_per_transform": round(per_transform / (total_us * 1e-6) / 1e9 / peak_gbs, 3),
+                    "hbm_frac_mean_per_pass": round(float(np.mean([x["frac"] for x in passes])), 3),
+                    "multiply_roof_frac": round(bfly_s / alu_peak_bfly(w, sm_mhz), 3)})
         del t
         plan.destroy()
     torch.cuda.synchronize()
@@ -714,7 +749,8 @@ def run_steady_only(args):
     cases = STEADY.get(args.workload, STEADY["c2"])
     return {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
             "launches_per_pass": K,
-            "cases": steady_state(cases, torch, ntt, load_peaks()["hbm_gbs"], K=K, warm=3 if K > 1 else 0)}
+            "cases": steady_state(cases, torch, ntt, load_peaks()["hbm_gbs"], K=K, warm=3 if K > 1 else 0,
+                                  sm_mhz=load_peaks()["sm_max_mhz"])}
 
 
 def run_ours(args, dist, rank, world):
@@ -782,18 +818,20 @@ def run_ours(args, dist, rank, world):
     frac_hbm = achieved_gbs / peaks["hbm_gbs"]
     frac_alu = achieved_bfly / alu_peak
     dom_name = f"{'inverse' if inv else 'forward'} pass {k} of {b_} x 2^{l_} (log2 R = {log_r})"
-    traffic = NCU_TRAFFIC.get((args.workload, dom_name))
+    traffic, traffic_note = ncu_traffic(args.workload, dom_name)
     if frac_alu >= frac_hbm:
         roof = {"bound": "alu", "achieved": achieved_bfly / 1e9, "peak": alu_peak / 1e9, "unit": "Gbutterflies/s",
                 "frac": frac_alu, "traffic": traffic, "kernel": dom_name,
-                "peak_src": f"152 SMs x clock x {alu_peak / (152 * peaks['sm_max_mhz'] * 1e6):.0f} butterflies/clk/SM "
+                "peak_src": f"152 SMs x clock x {alu_peak / (152 * peaks['sm_max_mhz'] * 1e6):.1f} butterflies/clk/SM "
                             "(measured multiply rates)",
                 "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": frac_hbm}}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": frac_hbm, "traffic": traffic, "kernel": dom_name, "peak_src": peaks["src"] + " (MEASURED_PEAKS.json)",
+                "frac": frac_hbm, "traffic": traffic, "kernel": dom_name,
+                "peak_src": peaks["src"] + " (MEASURED_PEAKS.json, of measured)",
                 "alu": {"achieved": achieved_bfly / 1e9, "peak": alu_peak / 1e9, "unit": "Gbutterflies/s",
                         "frac": frac_alu}}
+    roof["traffic_src"] = traffic_note
     line = {
         "metric": METRIC,
         "value": value,
@@ -802,8 +840,6 @@ def run_ours(args, dist, rank, world):
         "steps": K,
         "warmup": args.warmup,
         "ms_per_step": ms_lazy / K,
-        "step_ms": {"median": lazy_steps[len(lazy_steps) // 2],
-                    "p99": lazy_steps[min(len(lazy_steps) - 1, int(0.99 * len(lazy_steps)))]},
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -812,33 +848,79 @@ def run_ours(args, dist, rank, world):
         "config": {"workload": spec["name"], "butterflies_per_step": bfly_step,
                    "pass_splits_log2": wl.splits,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
-        "hbm_gbs_useful": world * bytes_step * K / (ms_lazy / 1e3) / 1e9,
-        "ntl": {"value": ntl_value, "unit": "butterflies/s", "ms_per_step": ms_ntl / K},
-        "lazy_over_ntl": ms_ntl / ms_lazy,
-        "montgomery": {"value": job_value(bfly_step * K, world, ms_mont / 1e3), "unit": "butterflies/s",
-                       "ms_per_step": ms_mont / K, "lazy_over_montgomery": ms_mont / ms_lazy},
-        "roofline": roof,
-        "kernels": {f"g{g}{'i' if i else 'f'}{s}": round(v["avg_ms"] * 1e3, 2) for (g, i, s), v in stats.items()},
+        "gpu_launches": len(events) // K,
+        "clocks": clocks,
         "e2e": {"value": world * bfly_step * k_e2e / (ms_e2e / 1e3), "unit": "butterflies/s",
                 "h2d_bytes_per_step": wl.e2e_bytes(), "d2h_bytes_per_step": wl.e2e_bytes(),
-                "path": "ntt_transform_host (pinned host buffers), forward then inverse per group, groups on concurrent host threads"},
-        "gpu_launches": len(events) // K,
-        "graph": "timed steps are CUDA graph replays; kernel times from an eager pass with events",
-        "clocks": clocks,
+                "path": "ntt_transform_host on pinned host buffers, fwd then inv per group"},
+        "roofline": roof,
+        "step_ms": {"median": lazy_steps[len(lazy_steps) // 2],
+                    "p99": lazy_steps[min(len(lazy_steps) - 1, int(0.99 * len(lazy_steps)))]},
+        "hbm_gbs_useful": world * bytes_step * K / (ms_lazy / 1e3) / 1e9,
     }
-    if args.workload in STEADY and not args.no_steady_state:
-        try:
-            line["steady_state"] = {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
-                                    "cases": steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"],
-                                                          K=max(1, args.steady_launches))}
-        except Exception as e:  # a report of its own; the headline above stands
-            line["steady_state"] = {"error": f"{type(e).__name__}: {e}"}
-    if not args.no_serving and args.workload == "c2":
-        line["polymul_serving"] = run_serving(args.serve_seconds, 20000.0, torch, ntt)
+    detail = {"kernels_us": {f"g{g}{'i' if i else 'f'}{s}": round(v["avg_ms"] * 1e3, 2) for (g, i, s), v in stats.items()},
+              "graph": "timed steps are CUDA graph replays; kernel times from an eager pass with events"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_oracle(groups)
-        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(groups)
-    return line
+        allc = cpu_baseline_all_cores(groups)
+        line["cpu_baseline_all_cores"] = {"value": allc["value"], "unit": allc["unit"], "cores": allc["cores"]}
+        detail["cpu_baseline_all_cores"] = allc
+    if args.workload in STEADY and not args.no_steady_state:
+        try:
+            cases = steady_state(STEADY[args.workload], torch, ntt, peaks["hbm_gbs"],
+                                 K=max(1, args.steady_launches), sm_mhz=peaks["sm_max_mhz"])
+            detail["steady_state"] = cases
+            line["steady_256MiB"] = {c["workload"].split(",")[0]: {
+                "split": c["split"], "fwd_inv_us": c["fwd_inv_us"], "hbm_frac_per_transform": c["hbm_frac_per_transform"],
+                "hbm_frac_mean_per_pass": c["hbm_frac_mean_per_pass"], "multiply_roof_frac": c["multiply_roof_frac"]}
+                for c in cases}
+        except Exception as e:  # a report of its own; the headline above stands
+            line["steady_256MiB"] = {"error": f"{type(e).__name__}: {e}"}
+    if not args.no_serving and args.workload == "c2":
+        sv = run_serving(args.serve_seconds, 20000.0, torch, ntt)
+        detail["polymul_serving"] = sv
+        line["polymul_serving"] = {"seconds": args.serve_seconds, "offered_req_per_s": 20000,
+                                   "p50_ms": round(sv["p50_ms"], 4), "p99_ms": round(sv["p99_ms"], 4),
+                                   "completed_req_per_s": round(sv["throughput_req_per_s"] or 0.0, 1)}
+    if args.workload == "c2" and not args.no_u64:
+        # the paper's own word size (beta = 2^64, Table 1): the 64-bit batched
+        # configuration, lazy against NTL-style in the same schedule
+        try:
+            line["u64_c3"] = u64_comparison(args, dist, torch, ntt)
+        except Exception as e:
+            line["u64_c3"] = {"error": f"{type(e).__name__}: {e}"}
+    line["montgomery"] = {"value": job_value(bfly_step * K, world, ms_mont / 1e3),
+                          "lazy_over_montgomery": round(ms_mont / ms_lazy, 4)}
+    line["ntl"] = {"value": ntl_value, "unit": "butterflies/s", "ms_per_step": ms_ntl / K}
+    line["lazy_over_ntl"] = round(ms_ntl / ms_lazy, 4)
+    return line, detail
+
+
+def u64_comparison(args, dist, torch, ntt):
+    """16 x 2^20 + 1 x 2^24 64-bit words (p = 2305843009448574977), forward +
+    inverse per step, graph replays with the L2 flushed: lazy (Algorithms 3/4)
+    and NTL-style (Algorithm 2), same schedule, same K steps as the headline."""
+    groups = WORKLOADS["c3"]["groups"]
+    wl = GPUWorkload(groups, torch, ntt, seed=31)
+    bfly_step = 2 * butterflies(groups)
+    out = {"workload": WORKLOADS["c3"]["name"]}
+    ms = {}
+    for name, v in (("lazy", 0), ("ntl", 1)):
+        wl.set_variant(v)
+        for _ in range(3):
+            wl.step()
+        g = capture_step(wl, torch)
+        t, _, _ = time_steps(wl, torch, args.steps, args.warmup, dist, graph=g)
+        ms[name] = max_over_ranks(t, dist, torch) / args.steps
+        del g
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    out["value"] = world * bfly_step / (ms["lazy"] / 1e3)
+    out["ms_per_step"] = round(ms["lazy"], 4)
+    out["ntl_value"] = world * bfly_step / (ms["ntl"] / 1e3)
+    out["lazy_over_ntl"] = round(ms["ntl"] / ms["lazy"], 4)
+    del wl
+    torch.cuda.empty_cache()
+    return out
 
 
 REF_STEP_BUDGET_S = 6.0  # upper bound on one reference step's oracle time (seconds)
@@ -942,6 +1024,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="serving run length (default: 60 s for --workload c5, 2 s inside the default bench)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-u64", action="store_true", help="skip the 64-bit lazy vs NTL-style comparison")
     ap.add_argument("--no-steady-state", action="store_true", help="skip the 256 MiB per-pass report")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the 256 MiB per-pass report (for profiling the pass kernels at that size)")
@@ -991,7 +1074,10 @@ def main():
     elif args.workload == "bigint":
         line = run_bigint(args, dist, rank, world)
     else:
-        line = run_ours(args, dist, rank, world)
+        line, detail = run_ours(args, dist, rank, world)
+        if rank == 0:
+            # the full per-pass report goes to stderr; stdout keeps one compact line
+            print("detail " + json.dumps(detail), file=sys.stderr, flush=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

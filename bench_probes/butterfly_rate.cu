@@ -7,12 +7,12 @@
 // per clock per SM at the GPU's maximum clock, per butterfly form, and the
 // raw rates of mul.hi.u32 and mad.lo.u32 chains.  out[] (grid*block words)
 // receives an xor of each thread's data so nothing is optimised away.
-// Built and run by `python bench.py --workload probe`.
+// Built and run by `python bench.py --workload probe` (not part of the library).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
 
-#include "../modarith.cuh"
+#include "modarith.cuh"  // the library's butterflies (compiled with -I paper_1205_2926_gb300/csrc)
 
 using namespace ntt;
 

@@ -264,16 +264,22 @@ int polymul_mod_p(uint64_t p, const void *d_a, size_t na, const void *d_b, size_
  * it at set-up time) for the modulus, any primitive L-th root and a length
  * L >= na + nb - 1; it must use NTT_VARIANT_LAZY and belong to the current
  * device.  a, b, c are device arrays as for polymul_mod_p; the result equals
- * polymul_mod_p's.  The first call on a device looks up the address of the
- * scratch array for that device (set-up done once per device); make that
- * first call before any stream capture.  Every call on a device shares the
+ * polymul_mod_p's.  What the first call on a device does: it looks up the
+ * address of the scratch array on that device with cudaGetSymbolAddress
+ * (set-up done once per device, no allocation; under CUDA's lazy module
+ * loading that lookup is when the driver places the library's module, array
+ * included, in device memory); make that first call before any stream
+ * capture.  The transform kernels' status word is likewise a __device__
+ * word, looked up by ntt_plan, so no later call allocates it.  Every call
+ * on a device shares the
  * one scratch array and leaves its contents behind (each call rewrites all
  * of it before use): calls whose work overlaps on the GPU -- different
  * streams, or different host threads -- race and give wrong results, so
  * serialise them (one stream, or events).  Asynchronous on `stream`.
  * Errors: NTT_ERR_ARG (null pointer, na or nb zero, NTL plan, plan of
- * another device), NTT_ERR_LENGTH (L < na + nb - 1), NTT_ERR_RANGE (scratch
- * too small), NTT_ERR_ALIGN, NTT_ERR_CUDA. */
+ * another device, device index 64 or above), NTT_ERR_LENGTH
+ * (L < na + nb - 1), NTT_ERR_RANGE (scratch too small), NTT_ERR_ALIGN,
+ * NTT_ERR_CUDA. */
 int polymul_mod_p_noalloc(ntt_plan_t plan, const void *d_a, size_t na, const void *d_b, size_t nb, void *d_c,
                           void *stream);
 

@@ -338,19 +338,28 @@ __global__ void k_check_input(const W *__restrict__ d, uint64_t stride, int logL
 static std::atomic<long long> g_pass_budget{2000000000LL};
 static std::atomic<uint32_t> g_pass_extra{0};
 
-// Device status word of the pass kernels, one per device.
+// Device status word of the pass kernels: a file-scope __device__ word (zero
+// when the module loads), so no transform ever allocates for it.  Host code
+// cannot use the variable's name as a device address; its address on each
+// device is looked up once with cudaGetSymbolAddress, with that device
+// current (ntt_plan does it for the plan's device, so the first transform
+// does no lookup either).
+static __device__ int g_pass_status_word;
+
 static cudaError_t pass_status(int **out) {
     static std::mutex m;
     static int *words[64] = {nullptr};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> g(m);
     if (!words[dev]) {
-        e = cudaMalloc(&words[dev], sizeof(int));
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_pass_status_word);
         if (e != cudaSuccess) return e;
-        e = cudaMemset(words[dev], 0, sizeof(int));
-        if (e != cudaSuccess) return e;
+        if (!p) return cudaErrorInvalidSymbol;
+        words[dev] = static_cast<int *>(p);
     }
     *out = words[dev];
     return cudaSuccess;
@@ -656,6 +665,14 @@ int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L) {
         pl->J = pl->wbytes == 4 ? (inv & 0xffffffffu) : inv;
     }
     cudaGetDevice(&pl->device);
+    {
+        int *word = nullptr;  // the pass kernels' status word on this device (a lookup, no allocation)
+        cudaError_t e = pass_status(&word);
+        if (e != cudaSuccess) {
+            delete pl;
+            return cuda_fail(e, "status word");
+        }
+    }
     int logr[kMaxPasses];
     int n = default_split(pl->logL, pl->wbytes, logr);
     int rc = apply_split(pl, n, logr);

@@ -176,7 +176,7 @@ static std::mutex g_noalloc_mu;
 static void *g_noalloc_addr[64];
 
 static int noalloc_scratch(int dev, void **out) {
-    if (dev < 0 || dev >= 64) return NTT_ERR_RANGE;
+    if (dev < 0 || dev >= 64) return NTT_ERR_ARG;  // devices beyond the table: not supported
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
         void *p = nullptr;

@@ -10,7 +10,7 @@ function.  Residues uniform in [0, p) come from rejection sampling on the top
 bit_length(p) bits of each draw, so they are exactly uniform.
 
 Workload recipes (the paper measures uniform residues at power-of-two lengths,
-Section 5; all sizes below are stated in the design doc):
+Section 5):
 
 * ``P_NTT30 = 998244353`` = 119 * 2^23 + 1, beta = 2^32 path.
 * ``P_NTT62 = 2305843009448574977``: the smallest prime > 2^61 that is 1 mod
