@@ -16,6 +16,18 @@
 
 using namespace ntt;
 
+// Alternative instruction forms of Algorithm 3's butterfly (same results):
+// the Shoup product written with explicit PTX multiplies, the final
+// low-product difference as one multiply-add by -p, and the additions in
+// different groupings.
+__device__ __forceinline__ uint32_t shoup_ptx(uint32_t t, uint32_t w, uint32_t wq, uint32_t negp) {
+    uint32_t q, r;
+    asm("mul.hi.u32 %0, %1, %2;" : "=r"(q) : "r"(wq), "r"(t));
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(w), "r"(t));
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(q), "r"(negp), "r"(r));
+    return r;
+}
+
 template <int F>
 __device__ __forceinline__ void bf(uint32_t &x, uint32_t &y, uint32_t w, uint32_t wq, uint32_t p, uint32_t p2) {
     if (F == 0) bfly_fwd_lazy(x, y, w, wq, p, p2);
@@ -23,6 +35,38 @@ __device__ __forceinline__ void bf(uint32_t &x, uint32_t &y, uint32_t w, uint32_
     if (F == 2) bfly_inv_lazy(x, y, w, wq, p, p2);
     if (F == 3) bfly_inv_ntl(x, y, w, wq, p);
     if (F == 4) bfly_fwd_lazy_w1(x, y, p2);
+    if (F == 5) {  // PTX Shoup product with mad by -p
+        const uint32_t s = umin(x + y, x + y - p2);
+        const uint32_t t = x - y + p2;
+        y = shoup_ptx(t, w, wq, 0u - p);
+        x = s;
+    }
+    if (F == 6) {  // t first, sum reduced by select
+        const uint32_t t = x - y + p2;
+        const uint32_t u = x + y;
+        x = u >= p2 ? u - p2 : u;
+        y = shoup_ptx(t, w, wq, 0u - p);
+    }
+    if (F == 7) {  // sum by a signed correction: u - 2p, plus 2p when negative
+        const uint32_t t = x - y + p2;
+        const int32_t d = (int32_t)(x + y - p2);
+        x = (uint32_t)d + (p2 & (uint32_t)(d >> 31));
+        y = shoup_ptx(t, w, wq, 0u - p);
+    }
+    if (F == 8) {  // Algorithm 2 with the PTX Shoup product
+        const uint32_t s = umin(x + y, x + y - p);
+        uint32_t t = x - y;
+        t = umin(t, t + p);
+        const uint32_t r = shoup_ptx(t, w, wq, 0u - p);
+        x = s;
+        y = umin(r, r - p);
+    }
+    if (F == 9) {  // inverse lazy (Algorithm 4) with the PTX Shoup product
+        const uint32_t a = umin(x, x - p2);
+        const uint32_t t = shoup_ptx(y, w, wq, 0u - p);
+        x = a + t;
+        y = a - t + p2;
+    }
 }
 
 template <int F>
@@ -54,13 +98,22 @@ __global__ void k_rate(uint32_t *out, int iters, uint32_t p, uint32_t w0, uint32
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// OP 0: mul.hi.u32; 1: mad.lo.u32; 2: the 64-bit product of two 32-bit
+// words (both halves used, one add to fold them).
 template <int OP>
 __global__ void k_mul(uint32_t *out, int iters, uint32_t seed) {
     uint32_t a[8], b = seed * 2654435761u + threadIdx.x;
     for (int i = 0; i < 8; ++i) a[i] = b + i * 977u;
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = OP == 0 ? __umulhi(a[i], b) ^ i : a[i] * b + 0x9E3779B9u;
+        for (int i = 0; i < 8; ++i) {
+            if (OP == 0) a[i] = __umulhi(a[i], b) ^ i;
+            if (OP == 1) a[i] = a[i] * b + 0x9E3779B9u;
+            if (OP == 2) {
+                const uint64_t r = (uint64_t)a[i] * b;
+                a[i] = (uint32_t)(r >> 32) + (uint32_t)r;
+            }
+        }
     }
     uint32_t s = 0;
     for (int i = 0; i < 8; ++i) s ^= a[i];
@@ -138,20 +191,27 @@ int main() {
     if (cudaMalloc(&out, (size_t)grid * block * sizeof(uint32_t)) != cudaSuccess) return 1;
     const uint32_t p = 998244353u, w0 = 12345u, wq0 = (uint32_t)(((uint64_t)w0 << 32) / p);
     const double clk = clk_khz * 1e3, bf = 48.0 * iters * (double)grid * block;
-    const char *names[5] = {"lazy_fwd", "ntl_fwd", "lazy_inv", "ntl_inv", "lazy_fwd_w1"};
-    double ms[5];
+    const char *names[10] = {"lazy_fwd", "ntl_fwd", "lazy_inv", "ntl_inv", "lazy_fwd_w1", "lazy_fwd_ptx",
+                             "lazy_fwd_ptx_sel", "lazy_fwd_ptx_sign", "ntl_fwd_ptx", "lazy_inv_ptx"};
+    double ms[10];
     ms[0] = timed(k_rate<0>, grid, block, out, iters, p, w0, wq0);
     ms[1] = timed(k_rate<1>, grid, block, out, iters, p, w0, wq0);
     ms[2] = timed(k_rate<2>, grid, block, out, iters, p, w0, wq0);
     ms[3] = timed(k_rate<3>, grid, block, out, iters, p, w0, wq0);
     ms[4] = timed(k_rate<4>, grid, block, out, iters, p, w0, wq0);
+    ms[5] = timed(k_rate<5>, grid, block, out, iters, p, w0, wq0);
+    ms[6] = timed(k_rate<6>, grid, block, out, iters, p, w0, wq0);
+    ms[7] = timed(k_rate<7>, grid, block, out, iters, p, w0, wq0);
+    ms[8] = timed(k_rate<8>, grid, block, out, iters, p, w0, wq0);
+    ms[9] = timed(k_rate<9>, grid, block, out, iters, p, w0, wq0);
     printf("{\"sms\": %d, \"max_clock_mhz\": %.0f", sms, clk / 1e6);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 10; ++i)
         printf(", \"%s_bfly_per_clk_sm\": %.3f", names[i], bf / (ms[i] * 1e-3) / clk / sms);
     const double mops = 8.0 * 4096 * (double)grid * block;
     const double t_hi = timed(k_mul<0>, grid, block, out, 4096, 1u), t_lo = timed(k_mul<1>, grid, block, out, 4096, 1u);
-    printf(", \"mulhi_per_clk_sm\": %.2f, \"madlo_per_clk_sm\": %.2f", mops / (t_hi * 1e-3) / clk / sms,
-           mops / (t_lo * 1e-3) / clk / sms);
+    const double t_wide = timed(k_mul<2>, grid, block, out, 4096, 1u);
+    printf(", \"mulhi_per_clk_sm\": %.2f, \"madlo_per_clk_sm\": %.2f, \"mulwide_plus_add_per_clk_sm\": %.2f",
+           mops / (t_hi * 1e-3) / clk / sms, mops / (t_lo * 1e-3) / clk / sms, mops / (t_wide * 1e-3) / clk / sms);
     uint64_t *out64 = nullptr;
     if (cudaMalloc(&out64, (size_t)grid * block * sizeof(uint64_t)) == cudaSuccess) {
         const uint64_t p64 = 2305843009448574977ull, w64 = 1234567ull;

@@ -64,6 +64,14 @@ extern "C" {
 #define NTT_VARIANT_NTL 1  /* Algorithm 2 and its fully reduced inverse (comparison baseline) */
 #define NTT_VARIANT_MONT 2 /* Algorithm 5 (Montgomery's product, lazy ranges) and its inverse
                               counterpart (Algorithm 4 with Montgomery's product) */
+#define NTT_VARIANT_MOLLER 3 /* Algorithm 2 in Moeller's form (end of Section 2): fully reduced,
+                                valid for any p < beta/phi */
+
+/* Largest modulus of each word size: p < beta/phi, phi = (1 + sqrt 5)/2 (Moeller's bound for
+ * the fully reduced butterfly; the redundant-residue variants need p < beta/4 and Algorithm 2
+ * as printed p < beta/2).  beta/phi is irrational, so p < beta/phi means p <= these values. */
+#define NTT_P_MAX_W32 2654435769u                /* floor(2^32 / phi) */
+#define NTT_P_MAX_W64 11400714819323198485ull    /* floor(2^64 / phi) */
 
 typedef struct ntt_plan_s *ntt_plan_t;
 
@@ -74,7 +82,8 @@ typedef struct ntt_plan_s *ntt_plan_t;
 int ntt_is_prime(uint64_t n, int *is_prime);
 
 /* Section 1 fixes "one of" the primitive L-th roots; this library's choice is
- * omega = g^((p-1)/L) with g the smallest quadratic non-residue mod p.
+ * omega = g^((p-1)/L) with g the smallest quadratic non-residue mod p (any
+ * odd prime p < 2^64).
  * Errors: NTT_ERR_MODULUS, NTT_ERR_LENGTH.  Host only. */
 int ntt_root_of_unity(uint64_t p, uint64_t L, uint64_t *omega);
 
@@ -84,24 +93,42 @@ int ntt_find_prime(uint64_t lo, int k, uint64_t *q);
 /* ------------------------------------------------------------------ plans */
 
 /* Make a plan for length-L transforms over F_p with root omega (Section 1).
- * Validates p (prime, < 2^62), L (power of two, 2 <= L, L | p-1) and omega
- * (omega^(L/2) = p-1, hence order exactly L), computes omega^-1 and L^-1, and
- * uploads the twiddle tables (W, W') of Algorithm 3/4 for both directions to
- * the current device.  *out receives the plan; the library owns its memory
- * until ntt_plan_destroy.  The variant starts as NTT_VARIANT_LAZY.
+ * Validates p (prime, <= NTT_P_MAX_W64), L (power of two, 2 <= L, L | p-1)
+ * and omega (omega^(L/2) = p-1, hence order exactly L), computes omega^-1 and
+ * L^-1, and uploads the twiddle tables (W, W') of Algorithms 2-4 for both
+ * directions to the current device.  Word size: 32-bit words for p < 2^30
+ * (beta/4 at beta = 2^32), 64-bit words otherwise.  The variant starts as
+ * NTT_VARIANT_LAZY when p < beta/4, else NTT_VARIANT_NTL when p < beta/2,
+ * else NTT_VARIANT_MOLLER.  *out receives the plan; the library owns its
+ * memory until ntt_plan_destroy.
  * Errors: NTT_ERR_ARG, NTT_ERR_MODULUS, NTT_ERR_LENGTH, NTT_ERR_ROOT,
  * NTT_ERR_RANGE (L > 2^26), NTT_ERR_NOMEM, NTT_ERR_CUDA. */
 int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L);
 
+/* ntt_plan with the word size chosen by the caller: word_bytes 4 (beta =
+ * 2^32, p <= NTT_P_MAX_W32) or 8 (beta = 2^64, p <= NTT_P_MAX_W64).  This is
+ * what Moeller's bound buys (end of Section 2): a prime between 2^30 and
+ * 2^32/phi still runs on 32-bit words with NTT_VARIANT_MOLLER (or
+ * NTT_VARIANT_NTL below 2^31), where the redundant-residue variants would need
+ * 64-bit words.  Default variant as for ntt_plan.
+ * Errors: as ntt_plan; NTT_ERR_ARG for another word_bytes, NTT_ERR_MODULUS
+ * for p beyond the word's bound. */
+int ntt_plan_words(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L, int word_bytes);
+
 /* Free a plan and its device tables (synchronises the device first). */
 int ntt_plan_destroy(ntt_plan_t plan);
 
-/* Select NTT_VARIANT_LAZY, NTT_VARIANT_NTL or NTT_VARIANT_MONT for later calls
- * on this plan.  The first selection of NTT_VARIANT_MONT builds the plan's
- * tables in Montgomery form (W' = beta W mod p, Algorithm 5's input), kept
- * beside the Shoup tables until the plan is destroyed or re-split; the
- * variant's input and output ranges are those of NTT_VARIANT_LAZY.
- * Errors: NTT_ERR_ARG, NTT_ERR_NOMEM. */
+/* Select NTT_VARIANT_LAZY, NTT_VARIANT_NTL, NTT_VARIANT_MONT or
+ * NTT_VARIANT_MOLLER for later calls on this plan.  The first selection of
+ * NTT_VARIANT_MONT builds the plan's tables in Montgomery form (W' = beta W
+ * mod p, Algorithm 5's input), kept beside the Shoup tables until the plan is
+ * destroyed or re-split; the variant's input and output ranges are those of
+ * NTT_VARIANT_LAZY.  NTT_VARIANT_MOLLER takes and returns fully reduced
+ * residues like NTT_VARIANT_NTL.  Each variant's modulus bound (beta the
+ * plan's word): LAZY and MONT p < beta/4 (Theorems 2-4), NTL p < beta/2
+ * (Theorem 1), MOLLER p < beta/phi.
+ * Errors: NTT_ERR_ARG, NTT_ERR_MODULUS (p beyond the variant's bound),
+ * NTT_ERR_NOMEM. */
 int ntt_plan_set_variant(ntt_plan_t plan, int variant);
 
 /* Read-only description of a plan.  word_bytes is 4 or 8; n_passes is the

@@ -20,6 +20,9 @@ from ._lib import NTTError, check
 VARIANT_LAZY = 0
 VARIANT_NTL = 1
 VARIANT_MONT = 2
+VARIANT_MOLLER = 3
+P_MAX_W32 = 2654435769  # floor(2^32 / phi): Moeller's bound for 32-bit words
+P_MAX_W64 = 11400714819323198485  # floor(2^64 / phi)
 
 
 def _ptr(x) -> int:
@@ -66,12 +69,16 @@ def find_prime(lo: int, k: int) -> int:
 
 
 class Plan:
-    """A device-resident plan for length-L transforms over F_p (ntt_plan)."""
+    """A device-resident plan for length-L transforms over F_p (ntt_plan, or
+    ntt_plan_words when the word size is given)."""
 
-    def __init__(self, p: int, omega: int, L: int):
+    def __init__(self, p: int, omega: int, L: int, word_bytes: int | None = None):
         lib = _lib.load()
         h = ctypes.c_void_p()
-        check(lib.ntt_plan(ctypes.byref(h), p, omega, L), "ntt_plan")
+        if word_bytes is None:
+            check(lib.ntt_plan(ctypes.byref(h), p, omega, L), "ntt_plan")
+        else:
+            check(lib.ntt_plan_words(ctypes.byref(h), p, omega, L, word_bytes), "ntt_plan_words")
         self.handle = h.value
         self.p, self.omega, self.L = p, omega, L
         self.word_bytes = self.info().word_bytes
@@ -111,8 +118,8 @@ class Plan:
             pass
 
 
-def ntt_plan(p: int, omega: int, L: int) -> Plan:
-    return Plan(p, omega, L)
+def ntt_plan(p: int, omega: int, L: int, word_bytes: int | None = None) -> Plan:
+    return Plan(p, omega, L, word_bytes)
 
 
 def ntt_forward_batch(plan: Plan, data, batch: int, stride_words: int | None = None, stream=None) -> None:

@@ -55,6 +55,7 @@ _SIGNATURES = {
     "ntt_root_of_unity": (c_int, [c_u64, c_u64, ctypes.POINTER(c_u64)]),
     "ntt_find_prime": (c_int, [c_u64, c_int, ctypes.POINTER(c_u64)]),
     "ntt_plan": (c_int, [ctypes.POINTER(c_void_p), c_u64, c_u64, c_u64]),
+    "ntt_plan_words": (c_int, [ctypes.POINTER(c_void_p), c_u64, c_u64, c_u64, c_int]),
     "ntt_plan_destroy": (c_int, [c_void_p]),
     "ntt_plan_set_variant": (c_int, [c_void_p, c_int]),
     "ntt_plan_set_checked": (c_int, [c_void_p, c_int]),

@@ -209,6 +209,57 @@ NTT_HD void bfly_inv_mont(W &x, W &y, W wm, W J, W p, W p2) {
     y = (W)(a - t + p2);
 }
 
+// Moeller's refinement of Algorithm 2 (end of Section 2): the fully reduced
+// butterfly for any p < beta/phi, phi = (1 + sqrt 5)/2, where X + Y may
+// exceed beta.  The subtraction takes its correction from the borrow
+// (X < Y); the addition is rewritten X - (p - Y), corrected by the borrow
+// X < p - Y.  The candidate remainder W T - Q p of Shoup's product is below
+// (1 + p/beta) p < phi p < beta, so its low word is exact and one
+// subtraction of p reduces it.  Compare-and-select forms: the unsigned
+// minimum of csub would need 2p <= beta here.
+template <typename W>
+NTT_HD W addmod_borrow(W x, W y, W p) {
+    const W t = (W)(p - y);
+    const W s = (W)(x - t);
+    return x < t ? (W)(s + p) : s;
+}
+
+template <typename W>
+NTT_HD W submod_borrow(W x, W y, W p) {
+    const W s = (W)(x - y);
+    return x < y ? (W)(s + p) : s;
+}
+
+// x - c if x >= c else x, for 0 <= x < min(2c, beta) (any c < beta).
+template <typename W>
+NTT_HD W csub_any(W x, W c) {
+    return x >= c ? (W)(x - c) : x;
+}
+
+template <typename W>
+NTT_HD void bfly_fwd_moller(W &x, W &y, W w, W wq, W p) {
+    const W s = addmod_borrow(x, y, p);
+    const W t = submod_borrow(x, y, p);
+    y = csub_any(shoup_mul(t, w, wq, p), p);
+    x = s;
+}
+
+// Inverse counterpart (X + WY, X - WY), fully reduced, p < beta/phi.
+template <typename W>
+NTT_HD void bfly_inv_moller(W &x, W &y, W w, W wq, W p) {
+    const W t = csub_any(shoup_mul(y, w, wq, p), p);
+    const W s = addmod_borrow(x, t, p);
+    y = submod_borrow(x, t, p);
+    x = s;
+}
+
+template <typename W>
+NTT_HD void bfly_moller_w1(W &x, W &y, W p) {
+    const W s = addmod_borrow(x, y, p);
+    y = submod_borrow(x, y, p);
+    x = s;
+}
+
 // Final normalisation (end of Section 3): [0, 2p) -> [0, p), [0, 4p) -> [0, p).
 template <typename W>
 NTT_HD W reduce2(W x, W p) {

@@ -140,7 +140,9 @@ extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_variant = pl->variant;
-    pl->variant = NTT_VARIANT_LAZY;
+    // time the lazy butterflies where the modulus allows them (the splits'
+    // relative cost is the same for every variant), else the plan's own
+    if (variant_fits(pl, NTT_VARIANT_LAZY)) pl->variant = NTT_VARIANT_LAZY;
     std::vector<int> best;
     float best_ms = 1e30f;
     int rc = NTT_OK;

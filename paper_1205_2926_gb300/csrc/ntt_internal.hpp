@@ -119,6 +119,9 @@ int enqueue_steps(ntt_plan_s *plan, int dir, void *data, size_t batch, size_t st
 // Whether a pass split is allowed for a transform of 2^logL words of wbytes.
 bool split_allowed(int logL, int wbytes, int n, const int *logr);
 
+// Whether a butterfly variant's modulus bound holds for the plan's p and word.
+bool variant_fits(const ntt_plan_s *pl, int variant);
+
 // Free the staging buffer, streams and events of ntt_transform_host.
 void release_host_pipeline(ntt_plan_s *plan);
 

@@ -62,10 +62,17 @@ namespace ntt {
 
 enum { DIR_FWD = 0, DIR_INV = 1 };
 // Butterfly variants: Algorithms 3-4 (lazy, Shoup's product), Algorithm 2 and
-// its fully reduced inverse (NTL-style), and Algorithm 5 with its inverse
+// its fully reduced inverse (NTL-style), Algorithm 5 with its inverse
 // counterpart (lazy ranges, Montgomery's product; the twiddle pairs then hold
-// (W, beta W mod p)).
-enum { VAR_LAZY = 0, VAR_NTL = 1, VAR_MONT = 2 };
+// (W, beta W mod p)), and Moeller's form of Algorithm 2 (fully reduced, any
+// p < beta/phi; end of Section 2).
+enum { VAR_LAZY = 0, VAR_NTL = 1, VAR_MONT = 2, VAR_MOLLER = 3 };
+
+// Variants whose values stay fully reduced in [0, p) between stages.
+template <int VAR>
+struct Reduced {
+    static constexpr bool ON = VAR == VAR_NTL || VAR == VAR_MOLLER;
+};
 enum { F_NORMALIZE = 1, F_MIDDLE = 2, F_MB = 4, F_TMA = 8 };
 
 constexpr int kThreads = 256;  // threads per CTA of the pass kernels
@@ -180,6 +187,8 @@ __device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2, W J) {
             bfly_fwd_lazy(x, y, w, wq, p, p2);
         else if (VAR == VAR_MONT)
             bfly_fwd_mont(x, y, wq, J, p, p2);
+        else if (VAR == VAR_MOLLER)
+            bfly_fwd_moller(x, y, w, wq, p);
         else
             bfly_fwd_ntl(x, y, w, wq, p);
     } else {
@@ -187,6 +196,8 @@ __device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2, W J) {
             bfly_inv_lazy(x, y, w, wq, p, p2);
         else if (VAR == VAR_MONT)
             bfly_inv_mont(x, y, wq, J, p, p2);
+        else if (VAR == VAR_MOLLER)
+            bfly_inv_moller(x, y, w, wq, p);
         else
             bfly_inv_ntl(x, y, w, wq, p);
     }
@@ -195,7 +206,9 @@ __device__ __forceinline__ void bfly(W &x, W &y, W w, W wq, W p, W p2, W J) {
 // Butterfly with W = 1 (no product; see modarith.cuh).
 template <typename W, int DIR, int VAR>
 __device__ __forceinline__ void bfly_w1(W &x, W &y, W p, W p2) {
-    if (DIR == DIR_FWD) {
+    if (VAR == VAR_MOLLER) {
+        bfly_moller_w1(x, y, p);
+    } else if (DIR == DIR_FWD) {
         if (VAR != VAR_NTL)
             bfly_fwd_lazy_w1(x, y, p2);
         else
@@ -211,8 +224,8 @@ __device__ __forceinline__ void bfly_w1(W &x, W &y, W p, W p2) {
 template <typename W, int VAR>
 __device__ __forceinline__ W mul_twiddle(W x, W w, W wq, W p, W J) {
     if (VAR == VAR_MONT) return mont_mul(x, wq, J, p);  // x < 4p -> [0, 2p)
-    W y = shoup_mul(x, w, wq, p);                       // any x < beta -> [0, 2p)
-    return VAR == VAR_NTL ? csub(y, p) : y;
+    W y = shoup_mul(x, w, wq, p);                       // any x < beta -> [0, 2p); x < p -> [0, phi p)
+    return Reduced<VAR>::ON ? csub(y, p) : y;
 }
 
 // ------------------------------------------------------- compile-time rounds
@@ -275,7 +288,7 @@ __device__ __forceinline__ void round_regs(W (&x)[1 << LE][Lanes<W>::V], const W
 
 template <typename W, int DIR, int VAR, int E>
 __device__ __forceinline__ void normalize(W (&x)[E][Lanes<W>::V], W p, W p2) {
-    if constexpr (VAR != VAR_NTL) {
+    if constexpr (!Reduced<VAR>::ON) {
 #pragma unroll
         for (int j = 0; j < E; ++j)
 #pragma unroll
@@ -324,7 +337,7 @@ __device__ __forceinline__ void last_stage_and_twiddle(W (&x)[E][Lanes<W>::V], u
     for (int j = 0; j < E; j += 2) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            if (VAR != VAR_NTL) {
+            if (!Reduced<VAR>::ON) {
                 const W s = (W)(x[j][v] + x[j + 1][v]);
                 const W t = (W)(x[j][v] - x[j + 1][v] + p2);
                 x[j][v] = s;
@@ -350,7 +363,7 @@ __device__ __forceinline__ void twiddle_and_first_stage(W (&x)[E][Lanes<W>::V], 
     for (int j = 0; j < E; j += 2) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            if (VAR != VAR_NTL) {
+            if (!Reduced<VAR>::ON) {
                 const W s = (W)(x[j][v] + x[j + 1][v]);
                 const W t = (W)(x[j][v] - x[j + 1][v] + p2);
                 x[j][v] = s;
@@ -882,7 +895,7 @@ __global__ void k_tiny(const PassArgs<W> a) {
     }
     for (int i = 0; i < L; ++i) {
         W v = x[i];
-        if (VAR != VAR_NTL) v = DIR == DIR_FWD ? reduce2(v, p) : reduce4(v, p, p2);
+        if (!Reduced<VAR>::ON) v = DIR == DIR_FWD ? reduce2(v, p) : reduce4(v, p, p2);
         d[i] = v;
     }
 }

@@ -8,12 +8,16 @@ cudaError_t launch_pass_u64_fwd_mont(const LaunchSpec &s, int kind, cudaStream_t
 cudaError_t launch_pass_u64_inv_lazy(const LaunchSpec &s, int kind, cudaStream_t st);
 cudaError_t launch_pass_u64_inv_ntl(const LaunchSpec &s, int kind, cudaStream_t st);
 cudaError_t launch_pass_u64_inv_mont(const LaunchSpec &s, int kind, cudaStream_t st);
+cudaError_t launch_pass_u64_fwd_moller(const LaunchSpec &s, int kind, cudaStream_t st);
+cudaError_t launch_pass_u64_inv_moller(const LaunchSpec &s, int kind, cudaStream_t st);
 
 cudaError_t launch_pass_u64(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st) {
-    if (dir == 0)
-        return var == 0 ? launch_pass_u64_fwd_lazy(s, kind, st)
-                        : var == 1 ? launch_pass_u64_fwd_ntl(s, kind, st) : launch_pass_u64_fwd_mont(s, kind, st);
-    return var == 0 ? launch_pass_u64_inv_lazy(s, kind, st)
-                    : var == 1 ? launch_pass_u64_inv_ntl(s, kind, st) : launch_pass_u64_inv_mont(s, kind, st);
+    switch (var) {
+        case 0: return dir == 0 ? launch_pass_u64_fwd_lazy(s, kind, st) : launch_pass_u64_inv_lazy(s, kind, st);
+        case 1: return dir == 0 ? launch_pass_u64_fwd_ntl(s, kind, st) : launch_pass_u64_inv_ntl(s, kind, st);
+        case 2: return dir == 0 ? launch_pass_u64_fwd_mont(s, kind, st) : launch_pass_u64_inv_mont(s, kind, st);
+        case 3: return dir == 0 ? launch_pass_u64_fwd_moller(s, kind, st) : launch_pass_u64_inv_moller(s, kind, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 }  // namespace ntt

@@ -398,11 +398,12 @@ static bool tma_map(const ntt_plan_s *pl, LaunchSpec &s, size_t batch) {
     return r == CUDA_SUCCESS;
 }
 
-static_assert(NTT_VARIANT_LAZY == VAR_LAZY && NTT_VARIANT_NTL == VAR_NTL && NTT_VARIANT_MONT == VAR_MONT,
+static_assert(NTT_VARIANT_LAZY == VAR_LAZY && NTT_VARIANT_NTL == VAR_NTL && NTT_VARIANT_MONT == VAR_MONT &&
+                  NTT_VARIANT_MOLLER == VAR_MOLLER,
               "the C-ABI variant numbers select the kernel variants directly");
 
 static cudaError_t launch(const ntt_plan_s *pl, const LaunchSpec &s, int kind, int dir, cudaStream_t st) {
-    const int var = pl->variant;  // NTT_VARIANT_LAZY, _NTL or _MONT: 0, 1, 2
+    const int var = pl->variant;  // NTT_VARIANT_LAZY, _NTL, _MONT or _MOLLER: 0, 1, 2, 3
     return pl->wbytes == 4 ? launch_pass_u32(s, kind, dir, var, st) : launch_pass_u64(s, kind, dir, var, st);
 }
 
@@ -564,6 +565,23 @@ static bool geometry_ok(const ntt_plan_s &pl, int q, uint64_t batch, bool persis
     return true;
 }
 
+// Whether a butterfly variant's modulus bound holds for the plan's p and word
+// (beta = 2^(8 wbytes)): p < beta/4 for the redundant-residue variants
+// (Theorems 2-4), p < beta/2 for Algorithm 2 (Theorem 1), p < beta/phi for
+// Moeller's form (end of Section 2).
+bool variant_fits(const ntt_plan_s *pl, int variant) {
+    const int bits = pl->wbytes * 8;
+    const uint64_t quarter = 1ull << (bits - 2), half = 1ull << (bits - 1);
+    const uint64_t golden = bits == 32 ? (uint64_t)NTT_P_MAX_W32 : (uint64_t)NTT_P_MAX_W64;
+    switch (variant) {
+        case NTT_VARIANT_LAZY:
+        case NTT_VARIANT_MONT: return pl->p < quarter;
+        case NTT_VARIANT_NTL: return pl->p < half;
+        case NTT_VARIANT_MOLLER: return pl->p <= golden;
+        default: return false;
+    }
+}
+
 }  // namespace ntt
 
 using namespace ntt;
@@ -621,7 +639,7 @@ int ntt_is_prime(uint64_t n, int *is_prime) {
 
 int ntt_root_of_unity(uint64_t p, uint64_t L, uint64_t *omega) {
     if (!omega) return NTT_ERR_ARG;
-    if (p < 3 || p >= (1ull << 62) || !nt::is_prime(p)) return NTT_ERR_MODULUS;
+    if (p < 3 || !nt::is_prime(p)) return NTT_ERR_MODULUS;
     if (L < 1 || (L & (L - 1)) || (p - 1) % L) return NTT_ERR_LENGTH;
     const uint64_t g = nt::smallest_qnr(p);
     *omega = nt::powmod(g, (p - 1) / L, p);
@@ -642,10 +660,12 @@ int ntt_find_prime(uint64_t lo, int k, uint64_t *q) {
     return NTT_ERR_RANGE;
 }
 
-int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L) {
+int ntt_plan_words(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L, int word_bytes) {
     if (!out) return NTT_ERR_ARG;
     *out = nullptr;
-    if (p < 3 || p >= (1ull << 62) || !nt::is_prime(p)) return NTT_ERR_MODULUS;
+    if (word_bytes != 4 && word_bytes != 8) return NTT_ERR_ARG;
+    const uint64_t pmax = word_bytes == 4 ? (uint64_t)NTT_P_MAX_W32 : (uint64_t)NTT_P_MAX_W64;
+    if (p < 3 || p > pmax || !nt::is_prime(p)) return NTT_ERR_MODULUS;
     if (L < 2 || (L & (L - 1))) return NTT_ERR_LENGTH;
     if (L > (1ull << 26)) return NTT_ERR_RANGE;
     if ((p - 1) % L) return NTT_ERR_LENGTH;
@@ -658,7 +678,10 @@ int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L) {
     pl->L = L;
     pl->L_inv = nt::powmod(L % p, p - 2, p);
     pl->logL = ilog2u(L);
-    pl->wbytes = p < (1ull << 30) ? 4 : 8;
+    pl->wbytes = word_bytes;
+    pl->variant = variant_fits(pl, NTT_VARIANT_LAZY)  ? NTT_VARIANT_LAZY
+                  : variant_fits(pl, NTT_VARIANT_NTL) ? NTT_VARIANT_NTL
+                                                      : NTT_VARIANT_MOLLER;
     {
         uint64_t inv = 1;  // p^-1 mod 2^64 by Newton's iteration (p odd); its low word is p^-1 mod 2^32
         for (int i = 0; i < 6; ++i) inv *= 2 - p * inv;
@@ -685,6 +708,10 @@ int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L) {
     return NTT_OK;
 }
 
+int ntt_plan(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L) {
+    return ntt_plan_words(out, p, omega, L, p < (1ull << 30) ? 4 : 8);
+}
+
 int ntt_plan_destroy(ntt_plan_t pl) {
     if (!pl) return NTT_ERR_ARG;
     cudaDeviceSynchronize();
@@ -696,8 +723,8 @@ int ntt_plan_destroy(ntt_plan_t pl) {
 }
 
 int ntt_plan_set_variant(ntt_plan_t pl, int variant) {
-    if (!pl || (variant != NTT_VARIANT_LAZY && variant != NTT_VARIANT_NTL && variant != NTT_VARIANT_MONT))
-        return NTT_ERR_ARG;
+    if (!pl || variant < NTT_VARIANT_LAZY || variant > NTT_VARIANT_MOLLER) return NTT_ERR_ARG;
+    if (!variant_fits(pl, variant)) return NTT_ERR_MODULUS;
     if (variant == NTT_VARIANT_MONT && !pl->mont) {
         std::lock_guard<std::mutex> lk(pl->mu);
         int rc = build_tables_form(pl, true);
@@ -755,7 +782,8 @@ int ntt_check_input(ntt_plan_t pl, int inverse, const void *d_data, size_t batch
         }
     }
     unsigned long long *word = static_cast<unsigned long long *>(pl->check_word);
-    const uint64_t bound = pl->variant == NTT_VARIANT_NTL ? pl->p : (inverse ? 4 : 2) * pl->p;
+    const bool reduced = pl->variant == NTT_VARIANT_NTL || pl->variant == NTT_VARIANT_MOLLER;
+    const uint64_t bound = reduced ? pl->p : (inverse ? 4 : 2) * pl->p;
     const uint64_t total = (uint64_t)batch * pl->L;
     const unsigned grid = (unsigned)std::min<uint64_t>((total + 255) / 256, 152 * 8);
     e = cudaMemsetAsync(word, 0xff, sizeof(unsigned long long), st);

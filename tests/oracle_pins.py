@@ -26,7 +26,10 @@ import numpy as np
 
 from paper_1205_2926_gb300.inputs import uniform_residues
 
-SMALL_PRIMES = [17, 97, 257, 7681, 12289, 998244353, 1073479681, 2305843009448574977]
+# ... plus two primes in Moeller's range beta/2 < p < beta/phi (end of Section 2) for 32- and 64-bit
+# words, where the oracle's additions must not overflow 64 bits
+SMALL_PRIMES = [17, 97, 257, 7681, 12289, 998244353, 1073479681, 2305843009448574977, 2649751553,
+                11400714819167322113]
 
 
 def v2(n: int) -> int:
