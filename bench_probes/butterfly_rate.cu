@@ -61,6 +61,65 @@ __device__ __forceinline__ void bf(uint32_t &x, uint32_t &y, uint32_t w, uint32_
         x = s;
         y = umin(r, r - p);
     }
+    if (F == 10) {  // Algorithm 3 written out in PTX, minimum form
+        asm("{\n .reg .u32 u, s2, t, q, r;\n"
+            " add.u32 u, %0, %1;\n sub.u32 s2, u, %4;\n"
+            " sub.u32 t, %0, %1;\n add.u32 t, t, %4;\n"
+            " mul.hi.u32 q, %3, t;\n mul.lo.u32 r, %2, t;\n mad.lo.u32 %1, q, %5, r;\n"
+            " min.u32 %0, u, s2;\n}"
+            : "+r"(x), "+r"(y)
+            : "r"(w), "r"(wq), "r"(p2), "r"(0u - p));
+    }
+    if (F == 11) {  // PTX, compare-and-select form of the sum
+        asm("{\n .reg .u32 u, s2, t, q, r;\n .reg .pred g;\n"
+            " add.u32 u, %0, %1;\n sub.u32 t, %0, %1;\n add.u32 t, t, %4;\n"
+            " mul.hi.u32 q, %3, t;\n mul.lo.u32 r, %2, t;\n mad.lo.u32 %1, q, %5, r;\n"
+            " setp.ge.u32 g, u, %4;\n sub.u32 s2, u, %4;\n selp.u32 %0, s2, u, g;\n}"
+            : "+r"(x), "+r"(y)
+            : "r"(w), "r"(wq), "r"(p2), "r"(0u - p));
+    }
+    if (F == 12) {  // PTX, X - Y + 2p as X + (2p - Y), sum by minimum
+        asm("{\n .reg .u32 u, s2, t, q, r;\n"
+            " sub.u32 t, %4, %1;\n add.u32 t, t, %0;\n add.u32 u, %0, %1;\n sub.u32 s2, u, %4;\n"
+            " mul.hi.u32 q, %3, t;\n mul.lo.u32 r, %2, t;\n mad.lo.u32 %1, q, %5, r;\n"
+            " min.u32 %0, u, s2;\n}"
+            : "+r"(x), "+r"(y)
+            : "r"(w), "r"(wq), "r"(p2), "r"(0u - p));
+    }
+    if (F == 13) {  // PTX, Shoup difference as an explicit subtraction of q p
+        asm("{\n .reg .u32 u, s2, t, q, r, qp;\n .reg .pred g;\n"
+            " add.u32 u, %0, %1;\n sub.u32 t, %0, %1;\n add.u32 t, t, %4;\n"
+            " mul.hi.u32 q, %3, t;\n mul.lo.u32 r, %2, t;\n mul.lo.u32 qp, q, %6;\n sub.u32 %1, r, qp;\n"
+            " setp.ge.u32 g, u, %4;\n sub.u32 s2, u, %4;\n selp.u32 %0, s2, u, g;\n}"
+            : "+r"(x), "+r"(y)
+            : "r"(w), "r"(wq), "r"(p2), "r"(0u - p), "r"(p));
+    }
+    if (F == 14) {  // Algorithm 4 in PTX, minimum form
+        asm("{\n .reg .u32 a, a2, q, r, tt;\n"
+            " sub.u32 a2, %0, %4;\n min.u32 a, %0, a2;\n"
+            " mul.hi.u32 q, %3, %1;\n mul.lo.u32 r, %2, %1;\n mad.lo.u32 tt, q, %5, r;\n"
+            " add.u32 %0, a, tt;\n sub.u32 %1, a, tt;\n add.u32 %1, %1, %4;\n}"
+            : "+r"(x), "+r"(y)
+            : "r"(w), "r"(wq), "r"(p2), "r"(0u - p));
+    }
+    if (F == 15) {  // Algorithm 4 in PTX, compare-and-select form
+        asm("{\n .reg .u32 a, a2, q, r, tt;\n .reg .pred g;\n"
+            " setp.ge.u32 g, %0, %4;\n sub.u32 a2, %0, %4;\n selp.u32 a, a2, %0, g;\n"
+            " mul.hi.u32 q, %3, %1;\n mul.lo.u32 r, %2, %1;\n mad.lo.u32 tt, q, %5, r;\n"
+            " add.u32 %0, a, tt;\n sub.u32 %1, a, tt;\n add.u32 %1, %1, %4;\n}"
+            : "+r"(x), "+r"(y)
+            : "r"(w), "r"(wq), "r"(p2), "r"(0u - p));
+    }
+    if (F == 16) {  // Algorithm 2 in PTX, compare-and-select corrections
+        asm("{\n .reg .u32 u, s2, t, t2, q, r, r2;\n .reg .pred g, h, k;\n"
+            " add.u32 u, %0, %1;\n sub.u32 t, %0, %1;\n"
+            " setp.lt.u32 h, %0, %1;\n add.u32 t2, t, %6;\n selp.u32 t, t2, t, h;\n"
+            " mul.hi.u32 q, %3, t;\n mul.lo.u32 r, %2, t;\n mad.lo.u32 r, q, %5, r;\n"
+            " setp.ge.u32 k, r, %6;\n sub.u32 r2, r, %6;\n selp.u32 %1, r2, r, k;\n"
+            " setp.ge.u32 g, u, %6;\n sub.u32 s2, u, %6;\n selp.u32 %0, s2, u, g;\n}"
+            : "+r"(x), "+r"(y)
+            : "r"(w), "r"(wq), "r"(p2), "r"(0u - p), "r"(p));
+    }
     if (F == 9) {  // inverse lazy (Algorithm 4) with the PTX Shoup product
         const uint32_t a = umin(x, x - p2);
         const uint32_t t = shoup_ptx(y, w, wq, 0u - p);
@@ -191,9 +250,11 @@ int main() {
     if (cudaMalloc(&out, (size_t)grid * block * sizeof(uint32_t)) != cudaSuccess) return 1;
     const uint32_t p = 998244353u, w0 = 12345u, wq0 = (uint32_t)(((uint64_t)w0 << 32) / p);
     const double clk = clk_khz * 1e3, bf = 48.0 * iters * (double)grid * block;
-    const char *names[10] = {"lazy_fwd", "ntl_fwd", "lazy_inv", "ntl_inv", "lazy_fwd_w1", "lazy_fwd_ptx",
-                             "lazy_fwd_ptx_sel", "lazy_fwd_ptx_sign", "ntl_fwd_ptx", "lazy_inv_ptx"};
-    double ms[10];
+    const char *names[17] = {"lazy_fwd", "ntl_fwd", "lazy_inv", "ntl_inv", "lazy_fwd_w1", "lazy_fwd_ptx",
+                             "lazy_fwd_ptx_sel", "lazy_fwd_ptx_sign", "ntl_fwd_ptx", "lazy_inv_ptx",
+                             "lazy_fwd_asm_min", "lazy_fwd_asm_sel", "lazy_fwd_asm_min2", "lazy_fwd_asm_subqp",
+                             "lazy_inv_asm_min", "lazy_inv_asm_sel", "ntl_fwd_asm_sel"};
+    double ms[17];
     ms[0] = timed(k_rate<0>, grid, block, out, iters, p, w0, wq0);
     ms[1] = timed(k_rate<1>, grid, block, out, iters, p, w0, wq0);
     ms[2] = timed(k_rate<2>, grid, block, out, iters, p, w0, wq0);
@@ -204,8 +265,15 @@ int main() {
     ms[7] = timed(k_rate<7>, grid, block, out, iters, p, w0, wq0);
     ms[8] = timed(k_rate<8>, grid, block, out, iters, p, w0, wq0);
     ms[9] = timed(k_rate<9>, grid, block, out, iters, p, w0, wq0);
+    ms[10] = timed(k_rate<10>, grid, block, out, iters, p, w0, wq0);
+    ms[11] = timed(k_rate<11>, grid, block, out, iters, p, w0, wq0);
+    ms[12] = timed(k_rate<12>, grid, block, out, iters, p, w0, wq0);
+    ms[13] = timed(k_rate<13>, grid, block, out, iters, p, w0, wq0);
+    ms[14] = timed(k_rate<14>, grid, block, out, iters, p, w0, wq0);
+    ms[15] = timed(k_rate<15>, grid, block, out, iters, p, w0, wq0);
+    ms[16] = timed(k_rate<16>, grid, block, out, iters, p, w0, wq0);
     printf("{\"sms\": %d, \"max_clock_mhz\": %.0f", sms, clk / 1e6);
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < 17; ++i)
         printf(", \"%s_bfly_per_clk_sm\": %.3f", names[i], bf / (ms[i] * 1e-3) / clk / sms);
     const double mops = 8.0 * 4096 * (double)grid * block;
     const double t_hi = timed(k_mul<0>, grid, block, out, 4096, 1u), t_lo = timed(k_mul<1>, grid, block, out, 4096, 1u);

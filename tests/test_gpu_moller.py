@@ -38,7 +38,9 @@ def run(plan, rows, inverse, torch, stride_extra=True):
     """Transform (batch, L) rows in a padded-stride batch; padding must stay."""
     batch, L = rows.shape
     dt = np.uint32 if plan.word_bytes == 4 else np.uint64
-    stride = L + (16 // plan.word_bytes if stride_extra else 0)
+    per16 = 16 // plan.word_bytes
+    stride = L + per16 if stride_extra else L
+    stride = (stride + per16 - 1) // per16 * per16  # rows start on 16-byte boundaries
     buf = np.full((batch, stride), np.iinfo(dt).max, dtype=dt)
     buf[:, :L] = rows.astype(dt)
     d = to_dev(buf, torch)
