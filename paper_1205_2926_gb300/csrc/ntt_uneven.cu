@@ -2,13 +2,15 @@
 // directions in ONE persistent kernel launch.
 //
 // Host side: descriptors are grouped by (plan, direction).  A group whose
-// plan runs in a single pass (L <= 2^12) becomes one "class task" whose rows
+// plan runs in a single pass (L <= 2^11) becomes one "class task" whose rows
 // are the transforms themselves (row addresses gathered in a device table),
 // so one CTA packs many short transforms that share twiddles.  Every
 // transform of a multi-pass plan becomes its own task with one stage per
 // pass.  Work items (one CTA's worth of one stage of one task) are listed in
-// dependency order: first-stage items of multi-pass tasks, then the
-// single-pass items, then later stages.
+// dependency order as a pipeline over chunks of multi-pass tasks: stage s of
+// chunk k beside stage 0 of chunk k + s, so that a later stage reads what the
+// previous one wrote shortly before (from L2), with the single-pass items
+// spread over the steps.
 //
 // Device side: each CTA of the persistent grid takes the next item from an
 // atomic counter.  An item of stage s > 0 waits until every item of stage
@@ -397,17 +399,50 @@ static int prepare(const ntt_desc_t *descs, size_t n, Prepared &pr) {
     }
     if (smem == (size_t)-1) return NTT_ERR_RANGE;  // a plan with a narrow column tile
     // items: stage 0 of multi-pass tasks, class tasks, then later stages
+    // Item order: a pipeline over chunks of multi-pass tasks (about
+    // kChunkBytes of transform data each).  Step k lists stage s of chunk
+    // k - s for every s, so a task's later stage follows its previous stage
+    // by one step: its inputs were written recently (still in L2; the whole
+    // batch's intermediate data would not be) and its dependencies are
+    // normally met when it is claimed.  The single-pass items, which depend
+    // on nothing, are spread evenly over the steps.  Every item still comes
+    // after all items it waits for, so the queue always drains.
     std::vector<UItem> items;
-    for (size_t ti = 0; ti < tasks.size(); ++ti)
-        if (!is_class[ti])
-            for (uint32_t c = 0; c < tasks[ti].st[0].units; ++c) items.push_back({(uint32_t)ti, 0, c});
-    for (size_t ti = 0; ti < tasks.size(); ++ti)
-        if (is_class[ti])
-            for (uint32_t c = 0; c < tasks[ti].st[0].units; ++c) items.push_back({(uint32_t)ti, 0, c});
-    for (int s = 1; s < kMaxPasses; ++s)
+    {
+        const uint64_t kChunkBytes = 24ull << 20;
+        std::vector<std::vector<uint32_t>> chunks(1);
+        uint64_t acc = 0;
+        int max_stages = 1;
+        for (size_t ti = 0; ti < tasks.size(); ++ti) {
+            if (is_class[ti]) continue;
+            const uint64_t bytes = 4ull << tasks[ti].logL;
+            if (acc > 0 && acc + bytes > kChunkBytes) {
+                chunks.emplace_back();
+                acc = 0;
+            }
+            chunks.back().push_back((uint32_t)ti);
+            acc += bytes;
+            max_stages = std::max<int>(max_stages, tasks[ti].nstages);
+        }
+        if (chunks.back().empty()) chunks.pop_back();
+        std::vector<UItem> class_items;
         for (size_t ti = 0; ti < tasks.size(); ++ti)
-            if (!is_class[ti] && s < tasks[ti].nstages)
-                for (uint32_t c = 0; c < tasks[ti].st[s].units; ++c) items.push_back({(uint32_t)ti, (uint32_t)s, c});
+            if (is_class[ti])
+                for (uint32_t c = 0; c < tasks[ti].st[0].units; ++c) class_items.push_back({(uint32_t)ti, 0, c});
+        const size_t nsteps = chunks.size() + (size_t)max_stages - 1;
+        size_t next_class = 0;
+        for (size_t k = 0; k < nsteps; ++k) {
+            for (int sg = 0; sg < max_stages; ++sg) {
+                if (k < (size_t)sg || k - sg >= chunks.size()) continue;
+                for (uint32_t ti : chunks[k - sg])
+                    if (sg < tasks[ti].nstages)
+                        for (uint32_t c = 0; c < tasks[ti].st[sg].units; ++c) items.push_back({ti, (uint32_t)sg, c});
+            }
+            const size_t upto = nsteps ? class_items.size() * (k + 1) / nsteps : class_items.size();
+            for (; next_class < upto; ++next_class) items.push_back(class_items[next_class]);
+        }
+        for (; next_class < class_items.size(); ++next_class) items.push_back(class_items[next_class]);
+    }
     // device copies
     cudaError_t e;
     if (!rowptrs.empty()) {
