@@ -347,12 +347,30 @@ typedef struct {
  * waits (bounded by a clock budget) for the tiles of the earlier pass of the
  * same transform.  Results are those of ntt_forward_batch/ntt_inverse_batch
  * on each transform alone.  Host-side preparation (descriptor upload) is
- * cached: calling again with the same descs array contents reuses it, so
- * the call can be captured in a CUDA graph after a first warm-up call.
+ * cached: calling again with the same descs array contents (and the plans'
+ * splits unchanged) reuses it, so the call can be captured in a CUDA graph
+ * after a first warm-up call.
  * Errors: NTT_ERR_ARG, NTT_ERR_RANGE (a 64-bit or NTL plan, or L > 2^22),
  * NTT_ERR_CUDA, NTT_ERR_TIMEOUT (reported by ntt_uneven_status when a wait
  * gave up). */
 int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream);
+
+/* Autotuner for uneven batches: pick the pass split of every multi-pass
+ * length class (plans with L > 2^11) by timing the persistent launch of this
+ * batch's layout, one class at a time (longest first) over every two-pass
+ * split the persistent kernel carries, the other classes fixed.  The chosen
+ * splits are applied to the plans (ntt_plan_set_split: later calls on those
+ * plans use them) and cached per (GPU model, word size, log L, log2 of the
+ * class's transform count) under "uneven/..." keys of the autotune cache
+ * file (NTT_AUTOTUNE_CACHE, else ~/.cache/ntt_gb300_autotune.json).  With
+ * use_cache != 0 and every class cached, the cached splits are applied
+ * without timing.  Timing runs on a scratch copy of the batch's layout
+ * (allocated and freed here; the caller's data are not touched) on `stream`,
+ * and synchronises it.  A prepared batch whose plans changed split since it
+ * was prepared is prepared again by the next ntt_execute_uneven.
+ * Errors: NTT_ERR_ARG, NTT_ERR_NOMEM, NTT_ERR_CUDA, and those of
+ * ntt_execute_uneven. */
+int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_cache, void *stream);
 
 /* Status word of the last ntt_execute_uneven on this device, read after the
  * stream has been synchronised: NTT_OK or NTT_ERR_TIMEOUT. */

@@ -195,15 +195,27 @@ def polymul_mod_p_noalloc(plan: Plan, a, na: int, b, nb: int, c, stream=None) ->
           "polymul_mod_p_noalloc")
 
 
-def ntt_execute_uneven(descs, stream=None) -> None:
-    """descs: sequence of (plan, device tensor or pointer, inverse flag)."""
+def _desc_array(descs):
     n = len(descs)
     arr = (_lib.Desc * n)()
     for i, (plan, data, inv) in enumerate(descs):
         arr[i].plan = plan.handle
         arr[i].d_data = _ptr(data)
         arr[i].inverse = int(bool(inv))
+    return arr, n
+
+
+def ntt_execute_uneven(descs, stream=None) -> None:
+    """descs: sequence of (plan, device tensor or pointer, inverse flag)."""
+    arr, n = _desc_array(descs)
     check(_lib.load().ntt_execute_uneven(arr, n, _stream(stream)), "ntt_execute_uneven")
+
+
+def ntt_uneven_autotune(descs, use_cache: bool = True, stream=None) -> None:
+    """Tune the pass split of each multi-pass length class of an uneven batch
+    inside the persistent launch (applied to the plans, cached); see the C header."""
+    arr, n = _desc_array(descs)
+    check(_lib.load().ntt_uneven_autotune(arr, n, int(use_cache), _stream(stream)), "ntt_uneven_autotune")
 
 
 def ntt_uneven_status() -> int:

@@ -188,3 +188,137 @@ extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int
     save_cache(m);
     return NTT_OK;
 }
+
+// ------------------------------------------------------------ uneven batches
+
+// The pass split of each multi-pass length class of an uneven batch, tuned
+// inside the persistent launch itself (the classes share the GPU, so the best
+// split of a class alone is not necessarily its best in the mix).  One round
+// of coordinate descent: classes in order of decreasing length, every allowed
+// two-pass split of the class timed with the others fixed.  Timed on a
+// scratch copy of the batch's layout, so the caller's data are not touched.
+extern "C" int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_cache, void *stream) {
+    if (!descs || n == 0) return NTT_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // distinct multi-pass plans, with the number of transforms using each
+    std::vector<ntt_plan_s *> plans;
+    std::vector<size_t> counts;
+    for (size_t i = 0; i < n; ++i) {
+        ntt_plan_s *pl = descs[i].plan;
+        if (!pl) return NTT_ERR_ARG;
+        if (pl->logL <= kMaxRowLog) continue;
+        auto it = std::find(plans.begin(), plans.end(), pl);
+        if (it == plans.end()) {
+            plans.push_back(pl);
+            counts.push_back(1);
+        } else {
+            ++counts[it - plans.begin()];
+        }
+    }
+    if (plans.empty()) return NTT_OK;
+    std::vector<size_t> order(plans.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return plans[a]->logL > plans[b]->logL; });
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::vector<std::string> keys(plans.size());
+    for (size_t i = 0; i < plans.size(); ++i) keys[i] = "uneven/" + tune_key(plans[i], counts[i]);
+    if (use_cache) {
+        auto m = load_cache();
+        bool all = true;
+        for (size_t i = 0; i < plans.size() && all; ++i) {
+            auto it = m.find(keys[i]);
+            all = it != m.end() && split_allowed(plans[i]->logL, plans[i]->wbytes, (int)it->second.size(),
+                                                 it->second.data());
+        }
+        if (all) {
+            for (size_t i = 0; i < plans.size(); ++i) {
+                const std::vector<int> &v = m[keys[i]];
+                bool same = (int)v.size() == plans[i]->npass;
+                for (size_t q = 0; same && q < v.size(); ++q) same = plans[i]->pass[q].logR == v[q];
+                if (!same) {
+                    int rc = ntt_plan_set_split(plans[i], (int)v.size(), v.data());
+                    if (rc) return rc;
+                }
+            }
+            return NTT_OK;
+        }
+    }
+    // scratch copy of the layout: each transform at a 16-byte-aligned offset
+    std::vector<ntt_desc_t> sd(descs, descs + n);
+    size_t words = 0;
+    for (size_t i = 0; i < n; ++i) words += (descs[i].plan->L + 3) & ~3ull;
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, std::max<size_t>(words, 4) * 4);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? NTT_ERR_NOMEM : cuda_fail(e, "uneven autotune buffer");
+    cudaMemsetAsync(buf, 0, std::max<size_t>(words, 4) * 4, st);
+    size_t off = 0;
+    for (size_t i = 0; i < n; ++i) {
+        sd[i].d_data = static_cast<uint32_t *>(buf) + off;
+        off += (descs[i].plan->L + 3) & ~3ull;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto time_batch = [&](float *ms) -> int {
+        for (int w = 0; w < 2; ++w) {
+            int rc = ntt_execute_uneven(sd.data(), n, st);
+            if (rc) return rc;
+        }
+        cudaEventRecord(e0, st);
+        const int reps = 5;
+        for (int r = 0; r < reps; ++r) {
+            int rc = ntt_execute_uneven(sd.data(), n, st);
+            if (rc) return rc;
+        }
+        cudaEventRecord(e1, st);
+        cudaError_t ee = cudaEventSynchronize(e1);
+        if (ee != cudaSuccess) return cuda_fail(ee, "uneven autotune timing");
+        int status = 0;
+        int rc = ntt_uneven_status(&status);
+        if (rc || status) return rc ? rc : status;
+        cudaEventElapsedTime(ms, e0, e1);
+        return NTT_OK;
+    };
+    int rc = NTT_OK;
+    for (size_t oi = 0; oi < order.size() && rc == NTT_OK; ++oi) {
+        ntt_plan_s *pl = plans[order[oi]];
+        std::vector<int> cur(pl->npass);
+        for (int q = 0; q < pl->npass; ++q) cur[q] = pl->pass[q].logR;
+        std::vector<int> best = cur;
+        float best_ms = 1e30f;
+        rc = time_batch(&best_ms);
+        if (rc) break;
+        for (int a = 3; a <= kMaxColLog; ++a) {
+            std::vector<int> cand = {a, pl->logL - a};
+            if (cand == cur || cand[1] > kMaxRowLog || !split_allowed(pl->logL, pl->wbytes, 2, cand.data())) continue;
+            rc = ntt_plan_set_split(pl, 2, cand.data());
+            if (rc) break;
+            float ms = 0;
+            const int trc = time_batch(&ms);
+            if (trc == NTT_ERR_RANGE) continue;  // a split the persistent kernel does not carry
+            if (trc) {
+                rc = trc;
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        if (rc) break;
+        rc = ntt_plan_set_split(pl, (int)best.size(), best.data());
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (rc) return rc;
+    auto m = load_cache();
+    for (size_t i = 0; i < plans.size(); ++i) {
+        std::vector<int> v(plans[i]->npass);
+        for (int q = 0; q < plans[i]->npass; ++q) v[q] = plans[i]->pass[q].logR;
+        m[keys[i]] = v;
+    }
+    save_cache(m);
+    return NTT_OK;
+}

@@ -256,8 +256,39 @@ __global__ void __launch_bounds__(kThreads, 3) k_uneven(const UTask *__restrict_
 
 // ----------------------------------------------------------------- host side
 
+// What a prepared batch copied from a plan: its split, variant and table
+// addresses.  A plan re-split (or given other tables) after the batch was
+// prepared no longer matches, and the batch is prepared again instead of
+// reading freed tables.
+struct PlanSig {
+    const ntt_plan_s *plan;
+    int npass, variant;
+    int logr[kMaxPasses];
+    const void *tw[2];
+    const void *mid[kMaxPasses][2][2];
+    bool operator==(const PlanSig &o) const { return memcmp(this, &o, sizeof(PlanSig)) == 0; }
+};
+
+static PlanSig plan_sig(const ntt_plan_s *pl) {
+    PlanSig g;
+    memset(&g, 0, sizeof(g));
+    g.plan = pl;
+    g.npass = pl->npass;
+    g.variant = pl->variant;
+    for (int d = 0; d < 2; ++d) g.tw[d] = pl->tw[d];
+    for (int q = 0; q < kMaxPasses; ++q) {
+        g.logr[q] = pl->pass[q].logR;
+        for (int d = 0; d < 2; ++d) {
+            g.mid[q][d][0] = pl->pass[q].ma[d];
+            g.mid[q][d][1] = pl->pass[q].mb[d];
+        }
+    }
+    return g;
+}
+
 struct Prepared {
     std::vector<ntt_desc_t> key;
+    std::vector<PlanSig> sigs;  // one per distinct plan of the batch
     UTask *d_tasks = nullptr;
     UItem *d_items = nullptr;
     uint32_t **d_rowptrs = nullptr;
@@ -287,9 +318,21 @@ static std::map<int, Prepared> g_prep;  // last prepared batch per device
 static long long g_wait_budget = 2000000000LL;  // clock cycles (about 1 s)
 static int g_stall_stage = -1;
 
-static bool same_key(const std::vector<ntt_desc_t> &k, const ntt_desc_t *d, size_t n) {
-    if (k.size() != n) return false;
-    return n == 0 || memcmp(k.data(), d, n * sizeof(ntt_desc_t)) == 0;
+static std::vector<PlanSig> batch_sigs(const ntt_desc_t *d, size_t n) {
+    std::vector<PlanSig> v;
+    std::vector<const ntt_plan_s *> seen;
+    for (size_t i = 0; i < n; ++i)
+        if (d[i].plan && std::find(seen.begin(), seen.end(), d[i].plan) == seen.end()) {
+            seen.push_back(d[i].plan);
+            v.push_back(plan_sig(d[i].plan));
+        }
+    return v;
+}
+
+static bool same_key(const Prepared &pr, const ntt_desc_t *d, size_t n) {
+    if (pr.key.size() != n) return false;
+    if (n && memcmp(pr.key.data(), d, n * sizeof(ntt_desc_t)) != 0) return false;
+    return pr.sigs == batch_sigs(d, n);
 }
 
 // Stage geometry of pass q of a plan, executed in direction dir as step i.
@@ -334,6 +377,7 @@ static UStage make_stage(const ntt_plan_s *pl, int dir, int i, uint32_t nrows_cl
 static int prepare(const ntt_desc_t *descs, size_t n, Prepared &pr) {
     pr.release();
     pr.key.assign(descs, descs + n);
+    pr.sigs = batch_sigs(descs, n);
     cudaGetDevice(&pr.device);
     // group by (plan, direction), preserving first appearance
     std::map<std::pair<ntt_plan_s *, int>, std::vector<size_t>> groups;
@@ -503,12 +547,13 @@ int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream) {
     int dev = 0;
     cudaGetDevice(&dev);
     Prepared &pr = g_prep[dev];
-    if (!same_key(pr.key, descs, n) || pr.device != dev || !pr.d_ctl) {
+    if (!same_key(pr, descs, n) || pr.device != dev || !pr.d_ctl) {
         cudaDeviceSynchronize();  // the previous batch's tables may still be in use
         int rc = prepare(descs, n, pr);
         if (rc) {
             pr.release();
             pr.key.clear();
+            pr.sigs.clear();
             return rc;
         }
     }
