@@ -356,12 +356,13 @@ typedef struct {
 int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream);
 
 /* Autotuner for uneven batches: pick the pass split of every multi-pass
- * length class (plans with L > 2^11) by timing the persistent launch of this
- * batch's layout, one class at a time (longest first) over every two-pass
- * split the persistent kernel carries, the other classes fixed.  The chosen
- * splits are applied to the plans (ntt_plan_set_split: later calls on those
- * plans use them) and cached per (GPU model, word size, log L, log2 of the
- * class's transform count) under "uneven/..." keys of the autotune cache
+ * length class (one class per length L > 2^11: every plan of that length,
+ * whatever its prime) by timing the persistent launch of this batch's layout,
+ * one class at a time (longest first) over every two-pass split the
+ * persistent kernel carries, the other classes fixed.  The chosen splits are
+ * applied to the plans (ntt_plan_set_split: later calls on those plans use
+ * them) and cached per (GPU model, word size, log L, log2 of the class's
+ * transform count) under "uneven/..." keys of the autotune cache
  * file (NTT_AUTOTUNE_CACHE, else ~/.cache/ntt_gb300_autotune.json).  With
  * use_cache != 0 and every class cached, the cached splits are applied
  * without timing.  Timing runs on a scratch copy of the batch's layout

@@ -193,52 +193,63 @@ extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int
 
 // The pass split of each multi-pass length class of an uneven batch, tuned
 // inside the persistent launch itself (the classes share the GPU, so the best
-// split of a class alone is not necessarily its best in the mix).  One round
-// of coordinate descent: classes in order of decreasing length, every allowed
-// two-pass split of the class timed with the others fixed.  Timed on a
-// scratch copy of the batch's layout, so the caller's data are not touched.
+// split of a class alone is not necessarily its best in the mix).  A class is
+// one transform length: every multi-pass plan of that length (whatever its
+// prime) takes the class's split.  One round of coordinate descent: classes
+// in order of decreasing length, every allowed two-pass split of the class
+// timed with the others fixed.  Timed on a scratch copy of the batch's
+// layout, so the caller's data are not touched.
 extern "C" int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_cache, void *stream) {
     if (!descs || n == 0) return NTT_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    // distinct multi-pass plans, with the number of transforms using each
-    std::vector<ntt_plan_s *> plans;
-    std::vector<size_t> counts;
+    struct Class {
+        int logL;
+        size_t count = 0;
+        std::vector<ntt_plan_s *> plans;
+        std::string key;
+    };
+    std::vector<Class> classes;
     for (size_t i = 0; i < n; ++i) {
         ntt_plan_s *pl = descs[i].plan;
         if (!pl) return NTT_ERR_ARG;
         if (pl->logL <= kMaxRowLog) continue;
-        auto it = std::find(plans.begin(), plans.end(), pl);
-        if (it == plans.end()) {
-            plans.push_back(pl);
-            counts.push_back(1);
-        } else {
-            ++counts[it - plans.begin()];
+        auto it = std::find_if(classes.begin(), classes.end(),
+                               [&](const Class &c) { return c.logL == pl->logL && c.plans[0]->wbytes == pl->wbytes; });
+        if (it == classes.end()) {
+            classes.emplace_back();
+            classes.back().logL = pl->logL;
+            it = classes.end() - 1;
         }
+        ++it->count;
+        if (std::find(it->plans.begin(), it->plans.end(), pl) == it->plans.end()) it->plans.push_back(pl);
     }
-    if (plans.empty()) return NTT_OK;
-    std::vector<size_t> order(plans.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return plans[a]->logL > plans[b]->logL; });
+    if (classes.empty()) return NTT_OK;
+    std::stable_sort(classes.begin(), classes.end(), [](const Class &a, const Class &b) { return a.logL > b.logL; });
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    std::vector<std::string> keys(plans.size());
-    for (size_t i = 0; i < plans.size(); ++i) keys[i] = "uneven/" + tune_key(plans[i], counts[i]);
+    for (Class &c : classes) c.key = "uneven/" + tune_key(c.plans[0], c.count);
+    auto apply = [&](Class &c, const std::vector<int> &v) -> int {
+        for (ntt_plan_s *pl : c.plans) {
+            bool same = (int)v.size() == pl->npass;
+            for (size_t q = 0; same && q < v.size(); ++q) same = pl->pass[q].logR == v[q];
+            if (!same) {
+                int rc = ntt_plan_set_split(pl, (int)v.size(), v.data());
+                if (rc) return rc;
+            }
+        }
+        return NTT_OK;
+    };
     if (use_cache) {
         auto m = load_cache();
         bool all = true;
-        for (size_t i = 0; i < plans.size() && all; ++i) {
-            auto it = m.find(keys[i]);
-            all = it != m.end() && split_allowed(plans[i]->logL, plans[i]->wbytes, (int)it->second.size(),
-                                                 it->second.data());
+        for (size_t i = 0; i < classes.size() && all; ++i) {
+            auto it = m.find(classes[i].key);
+            all = it != m.end() && split_allowed(classes[i].logL, classes[i].plans[0]->wbytes,
+                                                 (int)it->second.size(), it->second.data());
         }
         if (all) {
-            for (size_t i = 0; i < plans.size(); ++i) {
-                const std::vector<int> &v = m[keys[i]];
-                bool same = (int)v.size() == plans[i]->npass;
-                for (size_t q = 0; same && q < v.size(); ++q) same = plans[i]->pass[q].logR == v[q];
-                if (!same) {
-                    int rc = ntt_plan_set_split(plans[i], (int)v.size(), v.data());
-                    if (rc) return rc;
-                }
+            for (Class &c : classes) {
+                int rc = apply(c, m[c.key]);
+                if (rc) return rc;
             }
             return NTT_OK;
         }
@@ -280,18 +291,21 @@ extern "C" int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_ca
         return NTT_OK;
     };
     int rc = NTT_OK;
-    for (size_t oi = 0; oi < order.size() && rc == NTT_OK; ++oi) {
-        ntt_plan_s *pl = plans[order[oi]];
-        std::vector<int> cur(pl->npass);
-        for (int q = 0; q < pl->npass; ++q) cur[q] = pl->pass[q].logR;
+    for (size_t ci = 0; ci < classes.size() && rc == NTT_OK; ++ci) {
+        Class &c = classes[ci];
+        const ntt_plan_s *p0 = c.plans[0];
+        std::vector<int> cur(p0->npass);
+        for (int q = 0; q < p0->npass; ++q) cur[q] = p0->pass[q].logR;
+        rc = apply(c, cur);  // every plan of the class on one split to start
+        if (rc) break;
         std::vector<int> best = cur;
         float best_ms = 1e30f;
         rc = time_batch(&best_ms);
         if (rc) break;
         for (int a = 3; a <= kMaxColLog; ++a) {
-            std::vector<int> cand = {a, pl->logL - a};
-            if (cand == cur || cand[1] > kMaxRowLog || !split_allowed(pl->logL, pl->wbytes, 2, cand.data())) continue;
-            rc = ntt_plan_set_split(pl, 2, cand.data());
+            std::vector<int> cand = {a, c.logL - a};
+            if (cand == cur || cand[1] > kMaxRowLog || !split_allowed(c.logL, p0->wbytes, 2, cand.data())) continue;
+            rc = apply(c, cand);
             if (rc) break;
             float ms = 0;
             const int trc = time_batch(&ms);
@@ -306,7 +320,7 @@ extern "C" int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_ca
             }
         }
         if (rc) break;
-        rc = ntt_plan_set_split(pl, (int)best.size(), best.data());
+        rc = apply(c, best);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -314,10 +328,10 @@ extern "C" int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_ca
     cudaFree(buf);
     if (rc) return rc;
     auto m = load_cache();
-    for (size_t i = 0; i < plans.size(); ++i) {
-        std::vector<int> v(plans[i]->npass);
-        for (int q = 0; q < plans[i]->npass; ++q) v[q] = plans[i]->pass[q].logR;
-        m[keys[i]] = v;
+    for (const Class &c : classes) {
+        std::vector<int> v(c.plans[0]->npass);
+        for (int q = 0; q < c.plans[0]->npass; ++q) v[q] = c.plans[0]->pass[q].logR;
+        m[c.key] = v;
     }
     save_cache(m);
     return NTT_OK;

@@ -66,10 +66,13 @@ def test_uneven_autotune_per_length_class(tmp_path, monkeypatch):
     data = json.loads(cache.read_text())
     keys = [k for k in data if k.startswith("uneven/")]
     multi = {k: pl for k, pl in plans.items() if k[1] > (1 << 11)}
-    assert len(keys) == len(multi), (keys, list(multi))
+    lengths = sorted({k[1].bit_length() - 1 for k in multi})
+    assert sorted(int(k.split("/l")[1].split("/")[0]) for k in keys) == lengths, keys  # one class per length
     after = {k: list(pl.info().log_r)[:pl.info().n_passes] for k, pl in plans.items()}
     for k, pl in multi.items():
         assert sum(after[k]) == pl.info().log_L
+        same_len = [after[j] for j in multi if j[1] == k[1]]
+        assert all(s == after[k] for s in same_len), "plans of one length took different splits"
     changed = [k for k in multi if after[k] != before[k]]
     print("uneven splits changed by tuning:", {k[1]: (before[k], after[k]) for k in changed})
     ntt.ntt_execute_uneven(descs)
