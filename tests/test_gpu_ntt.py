@@ -270,8 +270,11 @@ def test_argument_errors():
         ntt.ntt_plan(p, (w * w) % p, 1024)  # order 512
     assert e.value.code == -3
     with pytest.raises(ntt.NTTError) as e:
-        ntt.ntt_plan((1 << 62) + 135, 3, 2)
+        ntt.ntt_plan(11400714819323198549, 3, 2)  # the first prime above floor(2^64/phi): no word fits it
     assert e.value.code == -1
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_plan((1 << 62) + 135, 3, 2)  # a prime in Moeller's range, but 3 is not -1 mod p
+    assert e.value.code == -3
     plan = ntt.ntt_plan(p, w, 1024)
     d = torch.zeros(4096, dtype=torch.int32, device="cuda")
     with pytest.raises(ntt.NTTError) as e:
