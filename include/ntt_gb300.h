@@ -346,10 +346,13 @@ typedef struct {
  * device-side atomic counter in dependency order, and a tile of a later pass
  * waits (bounded by a clock budget) for the tiles of the earlier pass of the
  * same transform.  Results are those of ntt_forward_batch/ntt_inverse_batch
- * on each transform alone.  Host-side preparation (descriptor upload) is
- * cached: calling again with the same descs array contents (and the plans'
- * splits unchanged) reuses it, so the call can be captured in a CUDA graph
- * after a first warm-up call.
+ * on each transform alone.  Host-side preparation (the work list's upload,
+ * synchronous) is cached per distinct batch (descs array contents and the
+ * plans' splits): calling again with the same batch reuses it, so the call
+ * can be captured in a CUDA graph after a first call outside the capture.
+ * Every batch prepared on a device stays prepared (a few bytes of device
+ * memory per work item) until ntt_uneven_release, so graphs that captured
+ * different batches stay valid side by side.
  * Errors: NTT_ERR_ARG, NTT_ERR_RANGE (a 64-bit or NTL plan, or L > 2^22),
  * NTT_ERR_CUDA, NTT_ERR_TIMEOUT (reported by ntt_uneven_status when a wait
  * gave up). */
@@ -372,6 +375,11 @@ int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream);
  * Errors: NTT_ERR_ARG, NTT_ERR_NOMEM, NTT_ERR_CUDA, and those of
  * ntt_execute_uneven. */
 int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_cache, void *stream);
+
+/* Free every batch prepared by ntt_execute_uneven on the current device
+ * (synchronises the device first).  Graphs that captured one of them must not
+ * be replayed afterwards.  Errors: NTT_ERR_CUDA. */
+int ntt_uneven_release(void);
 
 /* Status word of the last ntt_execute_uneven on this device, read after the
  * stream has been synchronised: NTT_OK or NTT_ERR_TIMEOUT. */

@@ -218,6 +218,11 @@ def ntt_uneven_autotune(descs, use_cache: bool = True, stream=None) -> None:
     check(_lib.load().ntt_uneven_autotune(arr, n, int(use_cache), _stream(stream)), "ntt_uneven_autotune")
 
 
+def ntt_uneven_release() -> None:
+    """Free every prepared uneven batch of the current device (see the C header)."""
+    check(_lib.load().ntt_uneven_release(), "ntt_uneven_release")
+
+
 def ntt_uneven_status() -> int:
     s = ctypes.c_int()
     check(_lib.load().ntt_uneven_status(ctypes.byref(s)), "ntt_uneven_status")

@@ -75,6 +75,7 @@ _SIGNATURES = {
     "polymul_mod_p_noalloc": (c_int, [c_void_p, c_void_p, c_size, c_void_p, c_size, c_void_p, c_void_p]),
     "ntt_execute_uneven": (c_int, [ctypes.POINTER(Desc), c_size, c_void_p]),
     "ntt_uneven_autotune": (c_int, [ctypes.POINTER(Desc), c_size, c_int, c_void_p]),
+    "ntt_uneven_release": (c_int, []),
     "ntt_uneven_status": (c_int, [ctypes.POINTER(c_int)]),
     "ntt_uneven_set_wait_budget": (c_int, [ctypes.c_longlong, c_int]),
     "ntt_pass_status": (c_int, [c_int, ctypes.POINTER(c_int)]),

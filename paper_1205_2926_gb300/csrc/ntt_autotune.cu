@@ -325,6 +325,8 @@ extern "C" int ntt_uneven_autotune(const ntt_desc_t *descs, size_t n, int use_ca
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
+    // the work lists prepared for the scratch layout (one per candidate) go with it
+    uneven_release_range(buf, static_cast<uint32_t *>(buf) + std::max<size_t>(words, 4));
     cudaFree(buf);
     if (rc) return rc;
     auto m = load_cache();

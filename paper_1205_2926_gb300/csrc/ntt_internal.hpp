@@ -122,6 +122,9 @@ bool split_allowed(int logL, int wbytes, int n, const int *logr);
 // Whether a butterfly variant's modulus bound holds for the plan's p and word.
 bool variant_fits(const ntt_plan_s *pl, int variant);
 
+// Free the prepared uneven batches whose transforms all lie in [lo, hi).
+void uneven_release_range(const void *lo, const void *hi);
+
 // Free the staging buffer, streams and events of ntt_transform_host.
 void release_host_pipeline(ntt_plan_s *plan);
 

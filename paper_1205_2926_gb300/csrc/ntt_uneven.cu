@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <map>
+#include <new>
 #include <mutex>
 #include <vector>
 
@@ -295,7 +296,11 @@ struct Prepared {
 };
 
 static std::mutex g_mu;
-static std::map<int, Prepared> g_prep;  // last prepared batch per device
+// Every batch prepared on a device stays prepared (its work list is small)
+// until ntt_uneven_release: graphs that captured different batches then stay
+// valid side by side, and preparing one batch never frees another's lists.
+static std::map<int, std::vector<Prepared *>> g_preps;
+static std::map<int, Prepared *> g_last;  // the batch launched last on each device
 static long long g_wait_budget = 2000000000LL;  // clock cycles (about 1 s)
 static int g_stall_stage = -1;
 
@@ -515,6 +520,29 @@ static int prepare(const ntt_desc_t *descs, size_t n, Prepared &pr) {
     return NTT_OK;
 }
 
+// Free the prepared batches whose transforms lie in [lo, hi) (a scratch
+// layout, such as the autotuner's, that nothing else launches).
+void uneven_release_range(const void *lo, const void *hi) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<Prepared *> &list = g_preps[dev];
+    std::vector<Prepared *> keep;
+    for (Prepared *pr : list) {
+        bool inside = !pr->key.empty();
+        for (const ntt_desc_t &d : pr->key)
+            inside = inside && (uintptr_t)d.d_data >= (uintptr_t)lo && (uintptr_t)d.d_data < (uintptr_t)hi;
+        if (inside) {
+            if (g_last[dev] == pr) g_last.erase(dev);
+            pr->release();
+            delete pr;
+        } else {
+            keep.push_back(pr);
+        }
+    }
+    list.swap(keep);
+}
+
 }  // namespace ntt
 
 using namespace ntt;
@@ -527,24 +555,46 @@ int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream) {
     std::lock_guard<std::mutex> lk(g_mu);
     int dev = 0;
     cudaGetDevice(&dev);
-    Prepared &pr = g_prep[dev];
-    if (!same_key(pr, descs, n) || pr.device != dev || !pr.d_ctl) {
-        cudaDeviceSynchronize();  // the previous batch's tables may still be in use
-        int rc = prepare(descs, n, pr);
+    std::vector<Prepared *> &list = g_preps[dev];
+    Prepared *pr = nullptr;
+    for (Prepared *q : list)
+        if (q->d_ctl && q->device == dev && same_key(*q, descs, n)) {
+            pr = q;
+            break;
+        }
+    if (!pr) {
+        pr = new (std::nothrow) Prepared();
+        if (!pr) return NTT_ERR_NOMEM;
+        int rc = prepare(descs, n, *pr);
         if (rc) {
-            pr.release();
-            pr.key.clear();
-            pr.sigs.clear();
+            pr->release();
+            delete pr;
             return rc;
         }
+        list.push_back(pr);
     }
-    cudaError_t e = cudaMemsetAsync(pr.d_done, 0, std::max<uint32_t>(1, pr.n_done) * sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(pr.d_ctl, 0, sizeof(UCtl), st);
+    g_last[dev] = pr;
+    cudaError_t e = cudaMemsetAsync(pr->d_done, 0, std::max<uint32_t>(1, pr->n_done) * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pr->d_ctl, 0, sizeof(UCtl), st);
     if (e != cudaSuccess) return cuda_fail(e, "uneven memset");
-    k_uneven<<<pr.grid, kThreads, pr.smem, st>>>(pr.d_tasks, pr.d_items, pr.n_items, pr.d_done, pr.d_ctl,
-                                                  g_wait_budget, g_stall_stage);
+    k_uneven<<<pr->grid, kThreads, pr->smem, st>>>(pr->d_tasks, pr->d_items, pr->n_items, pr->d_done, pr->d_ctl,
+                                                    g_wait_budget, g_stall_stage);
     e = cudaGetLastError();
     return e == cudaSuccess ? NTT_OK : cuda_fail(e, "k_uneven");
+}
+
+int ntt_uneven_release(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = cudaDeviceSynchronize();  // launches of these batches may still run
+    for (Prepared *pr : g_preps[dev]) {
+        pr->release();
+        delete pr;
+    }
+    g_preps[dev].clear();
+    g_last.erase(dev);
+    return e == cudaSuccess ? NTT_OK : cuda_fail(e, "uneven release");
 }
 
 int ntt_uneven_status(int *status) {
@@ -552,13 +602,13 @@ int ntt_uneven_status(int *status) {
     std::lock_guard<std::mutex> lk(g_mu);
     int dev = 0;
     cudaGetDevice(&dev);
-    auto it = g_prep.find(dev);
-    if (it == g_prep.end() || !it->second.d_ctl) {
+    auto it = g_last.find(dev);
+    if (it == g_last.end() || !it->second || !it->second->d_ctl) {
         *status = NTT_OK;
         return NTT_OK;
     }
     UCtl c;
-    cudaError_t e = cudaMemcpy(&c, it->second.d_ctl, sizeof(UCtl), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(&c, it->second->d_ctl, sizeof(UCtl), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "uneven status");
     *status = c.status;
     return NTT_OK;

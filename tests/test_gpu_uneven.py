@@ -81,6 +81,39 @@ def test_uneven_graph_capture_and_replay():
     b.check(rounds=3)
 
 
+def test_two_batches_in_two_graphs_stay_valid():
+    """Preparing a second batch keeps the first one's work list: graphs captured
+    on either replay correctly in any order; ntt_uneven_release frees both."""
+    torch = require_gpu()
+    b1 = Batch(uneven_batch_spec(seed=31, n=60, lmin=8, lmax=14), torch, seed=31)
+    b2 = Batch(uneven_batch_spec(seed=32, n=70, lmin=9, lmax=16), torch, seed=32)
+    s = torch.cuda.Stream()
+    graphs = []
+    for b in (b1, b2):
+        with torch.cuda.stream(s):
+            ntt.ntt_execute_uneven(b.descs(), stream=s)  # prepares this batch (outside any capture)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ntt.ntt_execute_uneven(b.descs(), stream=s)
+        graphs.append(g)
+    g1, g2 = graphs
+    g1.replay()
+    g2.replay()
+    g1.replay()
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    b1.check(rounds=3)
+    b2.check(rounds=2)
+    del g1, g2, graphs
+    ntt.ntt_uneven_release()
+    b3 = Batch(uneven_batch_spec(seed=33, n=40, lmin=8, lmax=13), torch, seed=33)
+    ntt.ntt_execute_uneven(b3.descs())
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    b3.check()
+
+
 def test_uneven_wait_times_out_with_status():
     """A dependency that never completes: the bounded wait gives up, the launch
     ends, the status says NTT_ERR_TIMEOUT and the context stays usable."""
