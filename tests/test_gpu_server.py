@@ -154,3 +154,40 @@ def test_page_locked_buffers_gathered_by_kernels():
         assert np.array_equal(c, outs[0])
     finally:
         sv.destroy()
+
+
+def test_full_degree_range_through_the_gather_scatter_path():
+    """The serving workload's whole degree range (up to 2^20, i.e. 2^21-point
+    products) through the page-locked gather/scatter path, mixed with small
+    requests: every result equals the oracle's product."""
+    torch = require_gpu()
+    rng = np.random.default_rng(44)
+    sizes = [((1 << 20) + 1, (1 << 20) + 1), ((1 << 19) + 1, (1 << 18) + 1), ((1 << 17) + 3, 65),
+             (1000, (1 << 20) + 1)] + [(int(rng.integers(64, 4096)), int(rng.integers(64, 4096))) for _ in range(12)]
+    reqs = []
+    for i, (na, nb) in enumerate(sizes):
+        a = uniform_residues(7700 + 2 * i, na, P_NTT30).astype(np.uint32)
+        b = uniform_residues(7701 + 2 * i, nb, P_NTT30).astype(np.uint32)
+        if i == 0:
+            a[:] = P_NTT30 - 1  # the top of the input range, every coefficient
+            b[:] = P_NTT30 - 1
+        reqs.append((a, b))
+    sv = ntt.Server(P_NTT30, max_coeffs=(1 << 20) + 1, mem_budget_bytes=1 << 30, n_streams=4)
+    try:
+        pinned = []
+        for a, b in reqs:
+            ta = torch.from_numpy(a.view(np.int32)).pin_memory()
+            tb = torch.from_numpy(b.view(np.int32)).pin_memory()
+            tc = torch.zeros(a.size + b.size - 1, dtype=torch.int32).pin_memory()
+            pinned.append((ta, tb, tc))
+        for ta, tb, tc in pinned:
+            assert sv.submit(ta.data_ptr(), ta.numel(), tb.data_ptr(), tb.numel(), tc.data_ptr())[0] == 0
+        assert sv.drain(120_000) == 0
+        st = sv.stats()
+        assert st.completed == len(reqs) and st.failed == 0 and st.direct_batches == st.batches
+        o = oracle.get()
+        for (a, b), (_, _, tc) in zip(reqs, pinned):
+            want = o.polymul_ntt(P_NTT30, a, b) if a.size * b.size > 4_000_000 else o.polymul_schoolbook(P_NTT30, a, b)
+            assert np.array_equal(tc.numpy().view(np.uint32).astype(np.uint64), want), (a.size, b.size)
+    finally:
+        sv.destroy()
