@@ -210,13 +210,58 @@ __global__ void k_rate64(uint64_t *out, int iters, uint64_t p, uint64_t w0, uint
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// High word of a 64 x 64-bit product without the low partial products: a1 b1 +
+// hi(a1 b0) + hi(a0 b1), at most 2 below the exact high word.
+__device__ __forceinline__ uint64_t mulhi64_trunc(uint64_t a, uint64_t b) {
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    return (uint64_t)a1 * b1 + __umulhi(a1, b0) + __umulhi(a0, b1);
+}
+
+// Algorithm 3 at 64 bits with the truncated quotient: Q' in [Q - 2, Q], so
+// W T - Q' p lies in [0, 4p) (p < beta/4) and one subtraction of 2p returns it
+// to [0, 2p).
+__global__ void k_rate64_trunc(uint64_t *out, int iters, uint64_t p, uint64_t w0, uint64_t wq0) {
+    uint64_t x[8][2];
+    for (int j = 0; j < 8; ++j)
+        for (int v = 0; v < 2; ++v) x[j][v] = (threadIdx.x * 37ull + j * 11ull + v) % p;
+    uint64_t w[7], wq[7];
+    for (int i = 0; i < 7; ++i) {
+        w[i] = w0 + i;
+        wq[i] = wq0 + i;
+    }
+    const uint64_t p2 = 2 * p;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int lb = 2; lb >= 0; --lb)
+#pragma unroll
+            for (int jl = 0; jl < (1 << lb); ++jl)
+#pragma unroll
+                for (int jh = 0; jh < 8; jh += (2 << lb))
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        uint64_t &xx = x[jh + jl][v], &yy = x[jh + jl + (1 << lb)][v];
+                        const uint64_t s = umin(xx + yy, xx + yy - p2);
+                        const uint64_t t = xx - yy + p2;
+                        const uint64_t q = mulhi64_trunc(wq[(1 << lb) - 1 + jl], t);
+                        const uint64_t r = w[(1 << lb) - 1 + jl] * t - q * p;
+                        yy = umin(r, r - p2);
+                        xx = s;
+                    }
+    }
+    uint64_t s = 0;
+    for (int j = 0; j < 8; ++j)
+        for (int v = 0; v < 2; ++v) s ^= x[j][v];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 template <int OP>
 __global__ void k_mul64(uint64_t *out, int iters, uint64_t seed) {
     uint64_t a[8], b = seed * 0x9E3779B97F4A7C15ull + threadIdx.x;
     for (int i = 0; i < 8; ++i) a[i] = b + i * 977ull;
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) a[i] = OP == 0 ? __umul64hi(a[i], b) ^ i : a[i] * b + 0x9E3779B97F4A7C15ull;
+        for (int i = 0; i < 8; ++i)
+            a[i] = OP == 0 ? __umul64hi(a[i], b) ^ i : OP == 2 ? mulhi64_trunc(a[i], b) ^ i : a[i] * b + 0x9E3779B97F4A7C15ull;
     }
     uint64_t s = 0;
     for (int i = 0; i < 8; ++i) s ^= a[i];
@@ -289,8 +334,12 @@ int main() {
         const double mops64 = 8.0 * 1024 * (double)grid * block;
         const double h64 = timed(k_mul64<0>, grid, block, out64, 1024, (uint64_t)1);
         const double l64 = timed(k_mul64<1>, grid, block, out64, 1024, (uint64_t)1);
+        const double ht64 = timed(k_mul64<2>, grid, block, out64, 1024, (uint64_t)1);
+        const double tt64 = timed(k_rate64_trunc, grid, block, out64, iters, p64, w64, wq64);
         printf(", \"lazy_fwd_u64_bfly_per_clk_sm\": %.3f, \"mulhi_u64_per_clk_sm\": %.2f, \"mullo_u64_per_clk_sm\": %.2f",
                bf64 / (t64 * 1e-3) / clk / sms, mops64 / (h64 * 1e-3) / clk / sms, mops64 / (l64 * 1e-3) / clk / sms);
+        printf(", \"mulhi_u64_trunc_per_clk_sm\": %.2f, \"lazy_fwd_u64_trunc_bfly_per_clk_sm\": %.3f",
+               mops64 / (ht64 * 1e-3) / clk / sms, bf64 / (tt64 * 1e-3) / clk / sms);
         cudaFree(out64);
     }
     printf(", \"error\": \"%s\"}\n", cudaGetErrorString(cudaGetLastError()));
