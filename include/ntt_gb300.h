@@ -131,6 +131,17 @@ int ntt_plan_destroy(ntt_plan_t plan);
  * NTT_ERR_NOMEM. */
 int ntt_plan_set_variant(ntt_plan_t plan, int variant);
 
+/* Choose the kernel of the plan's row pass (the last pass of the forward
+ * transform, the first of the inverse; the only pass when L <= 2^11) when its
+ * rows have 2^5..2^10 words: on != 0 runs one warp per row, each thread
+ * holding R/32 words in registers (stages of distance >= 32 inside a thread,
+ * one transpose through the warp's shared memory, the distances from R/32
+ * to 16 across lanes by warp shuffles, the rest inside a thread again); 0
+ * (the default) runs the radix-8 CTA rows of the other passes.  Results are
+ * identical (Algorithm 1's stages, the same butterflies).  Shorter or longer
+ * rows ignore the setting.  Errors: NTT_ERR_ARG. */
+int ntt_plan_set_warp_rows(ntt_plan_t plan, int on);
+
 /* Read-only description of a plan.  word_bytes is 4 or 8; n_passes is the
  * number of on-chip passes the transform is split into (four-step split of
  * Algorithm 1's stages); log_r[i] is log2 of pass i's sub-transform length;

@@ -91,6 +91,10 @@ class Plan:
     def set_variant(self, variant: int) -> None:
         check(_lib.load().ntt_plan_set_variant(self.handle, variant), "ntt_plan_set_variant")
 
+    def set_warp_rows(self, on: bool) -> None:
+        """Row passes of 2^5..2^10 words: one warp per row (register blocks, shuffles)."""
+        check(_lib.load().ntt_plan_set_warp_rows(self.handle, 1 if on else 0), "ntt_plan_set_warp_rows")
+
     def set_checked(self, on: bool) -> None:
         """Checked mode: transforms validate their input range first (NTT_ERR_INPUT)."""
         check(_lib.load().ntt_plan_set_checked(self.handle, 1 if on else 0), "ntt_plan_set_checked")

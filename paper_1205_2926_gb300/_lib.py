@@ -59,6 +59,7 @@ _SIGNATURES = {
     "ntt_plan_destroy": (c_int, [c_void_p]),
     "ntt_plan_set_variant": (c_int, [c_void_p, c_int]),
     "ntt_plan_set_checked": (c_int, [c_void_p, c_int]),
+    "ntt_plan_set_warp_rows": (c_int, [c_void_p, c_int]),
     "ntt_selftest_geometry": (c_int, [ctypes.POINTER(ctypes.c_longlong), ctypes.c_char_p, c_int]),
     "ntt_check_input": (c_int, [c_void_p, c_int, c_void_p, c_size, c_size, c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
     "ntt_plan_get_info": (c_int, [c_void_p, ctypes.POINTER(PlanInfo)]),

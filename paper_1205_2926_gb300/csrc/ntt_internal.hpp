@@ -62,6 +62,7 @@ struct ntt_plan_s {
     cudaStream_t hs_in = nullptr, hs_out = nullptr;
     cudaEvent_t hev_start = nullptr, hev_end = nullptr;
     cudaEvent_t hev_in[16] = {}, hev_done[16] = {};
+    bool warp_rows = false;      // row passes of 2^5..2^10 words run one warp per row (ntt_plan_set_warp_rows)
     bool checked = false;        // checked mode: validate input ranges before each transform
     void *check_word = nullptr;  // device word of ntt_check_input (allocated on first use)
     std::mutex mu;
@@ -69,7 +70,8 @@ struct ntt_plan_s {
 
 namespace ntt {
 
-// Launch of one pass (kind: 0 column pass, 1 row pass, 2 tiny length 2/4).
+// Launch of one pass (kind: 0 column pass, 1 row pass, 2 tiny length 2/4,
+// 3 row pass with one warp per row).
 // Defined per word type in ntt_pass_u32.cu / ntt_pass_u64.cu.
 struct LaunchSpec {
     void *data;

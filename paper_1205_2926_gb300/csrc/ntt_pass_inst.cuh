@@ -7,6 +7,7 @@
 
 #include "ntt_internal.hpp"
 #include "ntt_kernels.cuh"
+#include "ntt_warp.cuh"
 
 namespace ntt {
 
@@ -95,8 +96,35 @@ static cudaError_t launch_logr(const LaunchSpec &s, int logR, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+// Row pass with one warp per row (kind 3, 2^5 <= R <= 2^10): eight rows per
+// CTA, a grid-stride loop over the rows, shared memory for the warps' transposes.
+template <typename W, int DIR, int VAR, int LO, int HI>
+static cudaError_t launch_warp_logr(const LaunchSpec &s, cudaStream_t st) {
+    if (s.logR == LO) {
+        auto kern = k_warp_row<W, DIR, VAR, LO>;
+        const size_t smem = (size_t)kWarpRowsPerCta * ((1u << LO) + (1u << LO) / 32) * sizeof(W);
+        static int configured[64] = {0};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!configured[dev]) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            configured[dev] = 1;
+        }
+        const uint64_t ctas = (s.nrows + kWarpRowsPerCta - 1) / kWarpRowsPerCta;
+        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ctas, 152ull * 16));
+        kern<<<grid, kWarpRowsPerCta * 32, smem, st>>>(to_args<W>(s));
+        return cudaGetLastError();
+    }
+    if constexpr (LO < HI) return launch_warp_logr<W, DIR, VAR, LO + 1, HI>(s, st);
+    return cudaErrorInvalidValue;
+}
+
 template <typename W, int DIR, int VAR>
 static cudaError_t launch_kind(const LaunchSpec &s, int kind, cudaStream_t st) {
+    if (kind == 3) return launch_warp_logr<W, DIR, VAR, 5, 10>(s, st);
     if (kind == 0) return launch_logr<W, DIR, VAR, false, 3, kMaxColLog>(s, s.logR, st);
     if (kind == 1) return launch_logr<W, DIR, VAR, true, 3, kMaxRowLog>(s, s.logR, st);
     k_tiny<W, DIR, VAR><<<s.grid, 128, 0, st>>>(to_args<W>(s));

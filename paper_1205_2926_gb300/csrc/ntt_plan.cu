@@ -443,7 +443,8 @@ int enqueue_steps_roots(ntt_plan_s *pl, int dir, int roots, void *data, size_t b
         s.logS = ps.logS;
         s.flags = (i == n - 1) ? 1 : 0;  // F_NORMALIZE on the last executed pass
         tile_params(pl, q, batch, s);
-        const int kind = q == n - 1 ? 1 : 0;
+        int kind = q == n - 1 ? 1 : 0;
+        if (kind == 1 && pl->warp_rows && ps.logR >= 5 && ps.logR <= 10) kind = 3;  // one warp per row
         if (kind == 0) {
             s.logTA = ps.logTA;
             s.flags |= 2 | (ps.has_mb ? 4 : 0);  // F_MIDDLE, F_MB
@@ -801,6 +802,12 @@ int ntt_check_input(ntt_plan_t pl, int inverse, const void *d_data, size_t batch
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "check result");
     *first_bad = h == ~0ull ? -1 : (long long)h;
+    return NTT_OK;
+}
+
+int ntt_plan_set_warp_rows(ntt_plan_t pl, int on) {
+    if (!pl) return NTT_ERR_ARG;
+    pl->warp_rows = on != 0;
     return NTT_OK;
 }
 
