@@ -163,10 +163,13 @@ int ntt_plan_set_split(ntt_plan_t plan, int n_passes, const int *log_r);
 
 /* Autotuner: time every allowed pass split of this plan (forward + inverse
  * on a scratch batch of `batch` vectors, CUDA events, after warm-up), keep
- * the fastest, and store it in a JSON cache keyed by GPU name, word size,
- * log L and log2(batch) ($NTT_AUTOTUNE_CACHE, default
- * ~/.cache/ntt_gb300_autotune.json).  With use_cache != 0 a cached choice
- * for the same key is applied without timing.  log_r_out (may be NULL, else
+ * the fastest; then, when that split's row pass has 2^5..2^10 words, time
+ * it once with the radix-8 CTA rows and once with one warp per row
+ * (ntt_plan_set_warp_rows) and keep the faster body.  Both choices are
+ * stored in a JSON cache keyed by GPU name, word size, log L and
+ * log2(batch) ($NTT_AUTOTUNE_CACHE, default ~/.cache/ntt_gb300_autotune.json;
+ * the row body under the key + "/warp").  With use_cache != 0 a cached choice
+ * for the same key is applied without timing (no "/warp" entry: CTA rows).  log_r_out (may be NULL, else
  * room for 4 ints) receives the chosen split.  Allocates a scratch batch
  * and synchronises; call at set-up time.  Errors: NTT_ERR_ARG, NTT_ERR_NOMEM,
  * NTT_ERR_CUDA. */

@@ -1,5 +1,6 @@
-// ntt_autotune.cu -- picks the pass split of a plan by timing candidates on
-// the device, and remembers the choice in a small JSON cache file.
+// ntt_autotune.cu -- picks the pass split of a plan (and the body of its row
+// pass) by timing candidates on the device, and remembers the choice in a
+// small JSON cache file.
 //
 // A candidate is a split of log L into passes (the radix of each on-chip
 // sub-transform); the kernel geometry of each pass (tile width, rows per
@@ -119,11 +120,16 @@ extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int
     if (pl->logL <= 2) return NTT_OK;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const std::string key = tune_key(pl, batch);
+    // the row pass's body (radix-8 CTA rows, or one warp per row) is cached
+    // beside the split under key + "/warp"; an entry without it means CTA rows
+    const std::string wkey = key + "/warp";
     if (use_cache) {
         auto m = load_cache();
         auto it = m.find(key);
         if (it != m.end() && split_allowed(pl->logL, pl->wbytes, (int)it->second.size(), it->second.data())) {
             int rc = ntt_plan_set_split(pl, (int)it->second.size(), it->second.data());
+            auto wt = m.find(wkey);
+            pl->warp_rows = wt != m.end() && !wt->second.empty() && wt->second[0] != 0;
             if (rc == NTT_OK && log_r_out)
                 for (size_t i = 0; i < it->second.size(); ++i) log_r_out[i] = it->second[i];
             return rc;
@@ -140,6 +146,8 @@ extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int saved_variant = pl->variant;
+    const bool saved_warp = pl->warp_rows;
+    pl->warp_rows = false;  // splits are timed with the radix-8 rows
     // time the lazy butterflies where the modulus allows them (the splits'
     // relative cost is the same for every variant), else the plan's own
     if (variant_fits(pl, NTT_VARIANT_LAZY)) pl->variant = NTT_VARIANT_LAZY;
@@ -172,7 +180,37 @@ extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int
             best = cand;
         }
     }
+    // then the row pass's body for the chosen split: one warp per row against
+    // the radix-8 rows, when the rows are 2^5..2^10 words (measured: warp
+    // rows win for short rows in small, latency-bound launches)
+    bool warp = false;
+    const int row_log = best.empty() ? 0 : best.back();
+    if (rc == NTT_OK && row_log >= 5 && row_log <= 10) {
+        rc = ntt_plan_set_split(pl, (int)best.size(), best.data());
+        float ms[2] = {0, 0};
+        for (int w = 0; w < 2 && rc == NTT_OK; ++w) {
+            pl->warp_rows = w != 0;
+            for (int r = 0; r < 2; ++r) {
+                enqueue_transform(pl, 0, buf, batch, pl->L, st);
+                enqueue_transform(pl, 1, buf, batch, pl->L, st);
+            }
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 5; ++r) {
+                enqueue_transform(pl, 0, buf, batch, pl->L, st);
+                enqueue_transform(pl, 1, buf, batch, pl->L, st);
+            }
+            cudaEventRecord(e1, st);
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "autotune timing");
+                break;
+            }
+            cudaEventElapsedTime(&ms[w], e0, e1);
+        }
+        warp = rc == NTT_OK && ms[1] < ms[0];
+    }
     pl->variant = saved_variant;
+    pl->warp_rows = saved_warp;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);
@@ -181,10 +219,12 @@ extern "C" int ntt_plan_autotune(ntt_plan_t pl, size_t batch, int use_cache, int
     if (best.empty()) return NTT_ERR_ARG;
     rc = ntt_plan_set_split(pl, (int)best.size(), best.data());
     if (rc) return rc;
+    pl->warp_rows = warp;
     if (log_r_out)
         for (size_t i = 0; i < best.size(); ++i) log_r_out[i] = best[i];
     auto m = load_cache();
     m[key] = best;
+    m[wkey] = std::vector<int>{warp ? 1 : 0};
     save_cache(m);
     return NTT_OK;
 }

@@ -89,3 +89,31 @@ def test_uneven_autotune_per_length_class(tmp_path, monkeypatch):
     ntt.ntt_uneven_autotune(fdescs, use_cache=True)
     for k in multi:
         assert list(fresh[k].info().log_r)[:fresh[k].info().n_passes] == after[k]
+
+
+def test_autotune_picks_the_row_body(tmp_path, monkeypatch):
+    """For a short single-pass transform the tuner also times the row pass's
+    body (radix-8 CTA rows against one warp per row), caches the choice under
+    the "/warp" key, serves it from the cache, and the transform stays exact."""
+    torch = require_gpu()
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("NTT_AUTOTUNE_CACHE", str(cache))
+    o = oracle.get()
+    for logL, batch in ((6, 1), (8, 64)):
+        p, L = P_NTT30, 1 << logL
+        w = o.root_of_unity(p, L)
+        plan = ntt.ntt_plan(p, w, L)
+        split = plan.autotune(batch, use_cache=False)
+        assert sum(split) == logL
+        data = json.loads(cache.read_text())
+        wkeys = [k for k in data if k.endswith(f"/l{logL}/b{batch.bit_length() - 1}/warp")]
+        assert len(wkeys) == 1 and data[wkeys[0]] in ([0], [1]), data
+        plan2 = ntt.ntt_plan(p, w, L)
+        assert plan2.autotune(batch, use_cache=True) == split
+        a = batch_inputs(41 + logL, batch, L, p)
+        d = to_dev(a, torch)
+        ntt.ntt_forward_batch(plan2, d, batch)
+        torch.cuda.synchronize()
+        assert np.array_equal(from_dev(d, np.uint32).reshape(batch, L).astype(np.uint64),
+                              o.ntt_ref(p, w, a.astype(np.uint64)))
+        print(f"L=2^{logL} batch {batch}: split {split}, warp rows chosen = {data[wkeys[0]][0]}")
