@@ -96,27 +96,41 @@ static cudaError_t launch_logr(const LaunchSpec &s, int logR, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-// Row pass with one warp per row (kind 3, 2^5 <= R <= 2^10): eight rows per
-// CTA, a grid-stride loop over the rows, shared memory for the warps' transposes.
+// Row pass with one warp per row (kind 3, 2^5 <= R <= 2^10): eight warps per
+// CTA, each owning G consecutive rows at a time, a grid-stride loop over the
+// groups, shared memory for the warps' transposes.
+template <typename W, int DIR, int VAR, int LOGR, int G>
+static cudaError_t launch_warp_rows(const LaunchSpec &s, cudaStream_t st) {
+    auto kern = k_warp_row<W, DIR, VAR, LOGR, G>;
+    const size_t smem = (size_t)kWarpRowsPerCta * G * ((1u << LOGR) + (1u << LOGR) / 32) * sizeof(W);
+    static int configured[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = 1;
+    }
+    const uint64_t groups = (s.nrows + G - 1) / G;
+    const uint64_t ctas = (groups + kWarpRowsPerCta - 1) / kWarpRowsPerCta;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ctas, 152ull * 16));
+    kern<<<grid, kWarpRowsPerCta * 32, smem, st>>>(to_args<W>(s));
+    return cudaGetLastError();
+}
+
+// Several rows per warp once there are enough rows for two CTAs of such
+// groups per SM; one row per warp for short launches, whose time is the
+// length of one warp's chain.
 template <typename W, int DIR, int VAR, int LO, int HI>
 static cudaError_t launch_warp_logr(const LaunchSpec &s, cudaStream_t st) {
     if (s.logR == LO) {
-        auto kern = k_warp_row<W, DIR, VAR, LO>;
-        const size_t smem = (size_t)kWarpRowsPerCta * ((1u << LO) + (1u << LO) / 32) * sizeof(W);
-        static int configured[64] = {0};
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!configured[dev]) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-            configured[dev] = 1;
+        constexpr int G = WarpGroup<W, LO>::G;
+        if constexpr (G > 1) {
+            if (s.nrows >= (uint64_t)G * kWarpRowsPerCta * 152 * 2) return launch_warp_rows<W, DIR, VAR, LO, G>(s, st);
         }
-        const uint64_t ctas = (s.nrows + kWarpRowsPerCta - 1) / kWarpRowsPerCta;
-        const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ctas, 152ull * 16));
-        kern<<<grid, kWarpRowsPerCta * 32, smem, st>>>(to_args<W>(s));
-        return cudaGetLastError();
+        return launch_warp_rows<W, DIR, VAR, LO, 1>(s, st);
     }
     if constexpr (LO < HI) return launch_warp_logr<W, DIR, VAR, LO + 1, HI>(s, st);
     return cudaErrorInvalidValue;

@@ -99,3 +99,59 @@ def test_warp_rows_dit_dif_and_setting_off(p, logL):
         assert np.array_equal(got2, o.ntt_ref(p, wi, x.astype(np.uint64))), "DIF inverse"
         outs.append((got, got2))
     plan.destroy()
+
+
+def group_rows(wb, logR):
+    """Rows per warp of the batched warp-row kernel (several rows once a pass has
+    at least that many times 2 x 8 x 152 rows): up to 32 (32-bit) or 16 (64-bit)
+    words per thread, at most 8 rows."""
+    n = (1 << logR) // 32
+    words = 32 if wb == 4 else 16
+    return 1 if n >= words else min(8, words // n)
+
+
+@pytest.mark.parametrize("p,wb", [(P_NTT30, None), (P_NTT62, None), (P32M, 4)])
+@pytest.mark.parametrize("logR", [5, 6, 7, 8, 9])
+@pytest.mark.parametrize("last_of", [0, 6])
+def test_warp_rows_many_rows_per_warp(p, wb, logR, last_of):
+    """Passes with enough rows for several rows per warp (shared twiddle loads,
+    lane stages paired across rows), every variant: alone (last_of = 0), with a
+    ragged number of rows (a multiple of neither the rows per warp nor the warps
+    per CTA), and as the last pass of a [6, log R] split."""
+    torch = require_gpu()
+    o = oracle.get()
+    logL = logR + last_of
+    L = 1 << logL
+    if (p - 1) % L:
+        pytest.skip("L does not divide p-1")
+    w = o.root_of_unity(p, L)
+    plan = ntt.ntt_plan(p, w, L, word_bytes=wb)
+    if last_of:
+        plan.set_split([last_of, logR])
+    plan.set_warp_rows(True)
+    dt = np.uint32 if plan.word_bytes == 4 else np.uint64
+    g = group_rows(plan.word_bytes, logR)
+    if g == 1:
+        plan.destroy()
+        pytest.skip("one row per warp at this length and word size")
+    rows_needed = g * 2 * 8 * 152 + 3
+    batch = -(-rows_needed // (L >> logR))
+    if (batch * (L >> logR)) % g == 0:
+        batch += 1
+    try:
+        for v in variants_for(p, wb):
+            plan.set_variant(v)
+            top_f = p - 1 if v in (1, 3) else 2 * p - 1
+            top_i = p - 1 if v in (1, 3) else 4 * p - 1
+            a = batch_inputs(2400 + logL, batch, L, p).astype(np.uint64)
+            a[1, :] = top_f
+            a[-1, :] = top_f
+            got = run(plan, a, False, torch, dt)
+            assert np.array_equal(got, o.ntt_ref(p, w, a % np.uint64(p))), f"forward variant {v}"
+            y = batch_inputs(2500 + logL, batch, L, p).astype(np.uint64)
+            y[0, :] = top_i
+            y[-1, :] = top_i
+            got = run(plan, y, True, torch, dt)
+            assert np.array_equal(got, o.intt_ref(p, w, y % np.uint64(p))), f"inverse variant {v}"
+    finally:
+        plan.destroy()
