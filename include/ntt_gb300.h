@@ -136,10 +136,12 @@ int ntt_plan_set_variant(ntt_plan_t plan, int variant);
  * rows have 2^5..2^10 words: on != 0 runs one warp per row, each thread
  * holding R/32 words in registers (stages of distance >= 32 inside a thread,
  * one transpose through the warp's shared memory, the distances from R/32
- * to 16 across lanes by warp shuffles, the rest inside a thread again); 0
- * (the default) runs the radix-8 CTA rows of the other passes.  Results are
- * identical (Algorithm 1's stages, the same butterflies).  Shorter or longer
- * rows ignore the setting.  Errors: NTT_ERR_ARG. */
+ * to 16 across lanes by warp shuffles, the rest inside a thread again; in
+ * passes of many rows a warp owns several rows at once); 0 (the default)
+ * runs the radix-8 CTA rows of the other passes.  Results are identical
+ * (Algorithm 1's stages, the same butterflies).  Shorter or longer rows
+ * ignore the setting; ntt_plan_autotune sets it by timing.  Errors:
+ * NTT_ERR_ARG. */
 int ntt_plan_set_warp_rows(ntt_plan_t plan, int on);
 
 /* Read-only description of a plan.  word_bytes is 4 or 8; n_passes is the

@@ -104,8 +104,9 @@ class Plan:
         check(_lib.load().ntt_plan_set_split(self.handle, len(log_r), arr), "ntt_plan_set_split")
 
     def autotune(self, batch: int, use_cache: bool = True) -> list:
-        """Time every allowed pass split for this batch size, keep the fastest
-        (cached per GPU model and shape); returns the chosen split."""
+        """Time every allowed pass split for this batch size, keep the fastest,
+        then the row pass's body (CTA rows or one warp per row) for that split
+        (both cached per GPU model and shape); returns the chosen split."""
         out = (ctypes.c_int * 4)()
         check(_lib.load().ntt_plan_autotune(self.handle, batch, int(use_cache), out), "ntt_plan_autotune")
         return [v for v in out if v][: self.info().n_passes]
