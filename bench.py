@@ -512,6 +512,31 @@ def run_uneven(args, dist, rank, world):
     K = args.steps
     per = ms / K / 1e3
     gbs = nbytes / per / 1e9
+    # the same batch with the NTL-style butterflies (Algorithm 2), same splits
+    for pl in plans.values():
+        pl.set_variant(ntt.VARIANT_NTL)
+    with torch.cuda.stream(s):
+        ntt.ntt_execute_uneven(descs, stream=s)
+    torch.cuda.synchronize()
+    g_ntl = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g_ntl, stream=s):
+        ntt.ntt_execute_uneven(descs, stream=s)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        g_ntl.replay()
+    ev_ntl = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g_ntl.replay()
+        e1.record()
+        ev_ntl.append((e0, e1))
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    ms_ntl = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev_ntl), dist, torch)
+    for pl in plans.values():
+        pl.set_variant(ntt.VARIANT_LAZY)
     return {
         "metric": METRIC, "value": world * bfly / per, "unit": "butterflies/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms / K,
@@ -528,6 +553,8 @@ def run_uneven(args, dist, rank, world):
                      "per_pass": {"achieved": pass_bytes / per / 1e9, "frac": pass_bytes / per / 1e9 / peaks["hbm_gbs"],
                                   "note": "every word read and written once per pass (two passes above 2^11)"}},
         "gpu_launches": 1, "graph": "one CUDA graph replay per step", "clocks": clocks,
+        "ntl": {"value": world * bfly / (ms_ntl / K / 1e3), "unit": "butterflies/s", "ms_per_step": ms_ntl / K},
+        "lazy_over_ntl": round(ms_ntl / ms, 4),
     }
 
 

@@ -349,8 +349,9 @@ int bigint_mul(const uint32_t *d_a, size_t na, const uint32_t *d_b, size_t nb, u
 
 /* One transform of an uneven batch: its plan, its device vector (L words of
  * the plan's word type, 16-byte aligned) and its direction (0 forward,
- * 1 inverse).  Plans may differ in p and L; all must use 32-bit words and the
- * lazy variant, and live on the current device. */
+ * 1 inverse).  Plans may differ in p and L; all must use 32-bit words and one
+ * butterfly variant, NTT_VARIANT_LAZY (Algorithms 3-4) or NTT_VARIANT_NTL
+ * (Algorithm 2), and live on the current device. */
 typedef struct {
     ntt_plan_t plan;
     void *d_data;
@@ -369,7 +370,8 @@ typedef struct {
  * Every batch prepared on a device stays prepared (a few bytes of device
  * memory per work item) until ntt_uneven_release, so graphs that captured
  * different batches stay valid side by side.
- * Errors: NTT_ERR_ARG, NTT_ERR_RANGE (a 64-bit or NTL plan, or L > 2^22),
+ * Errors: NTT_ERR_ARG (also plans of different variants in one batch),
+ * NTT_ERR_RANGE (a 64-bit plan, a variant other than LAZY or NTL, L > 2^22),
  * NTT_ERR_CUDA, NTT_ERR_TIMEOUT (reported by ntt_uneven_status when a wait
  * gave up). */
 int ntt_execute_uneven(const ntt_desc_t *descs, size_t n, void *stream);

@@ -51,11 +51,15 @@ def test_uneven_small_mix():
     b.check()
 
 
-def test_uneven_full_workload_4096():
-    """4096 transforms, L = 2^8..2^16 log-uniform, three 30-bit primes, half inverse."""
+@pytest.mark.parametrize("variant", [0, 1])
+def test_uneven_full_workload_4096(variant):
+    """4096 transforms, L = 2^8..2^16 log-uniform, three 30-bit primes, half
+    inverse; lazy (Algorithms 3-4) and NTL-style (Algorithm 2) butterflies."""
     torch = require_gpu()
     spec = uneven_batch_spec()
     b = Batch(spec, torch)
+    for pl in b.plans.values():
+        pl.set_variant(variant)
     ntt.ntt_execute_uneven(b.descs())
     torch.cuda.synchronize()
     assert ntt.ntt_uneven_status() == 0
@@ -149,3 +153,35 @@ def test_uneven_rejects_unsupported():
     with pytest.raises(ntt.NTTError) as e:
         ntt.ntt_execute_uneven([(plan, t32.data_ptr() + 4, False)])
     assert e.value.code == -8
+
+
+def test_uneven_ntl_variant_and_variant_rules():
+    """The persistent launch with the NTL-style butterflies (Algorithm 2): the
+    same results as the oracle, including rows of p - 1 (the top of its input
+    interval [0, p)); a batch mixing variants is refused (NTT_ERR_ARG), and the
+    Montgomery variant is not carried (NTT_ERR_RANGE)."""
+    torch = require_gpu()
+    spec = uneven_batch_spec(seed=13, n=300, lmin=3, lmax=16)
+    b = Batch(spec, torch, seed=17)
+    for i, (d, a, t) in enumerate(b.items):
+        if i % 5 == 0:  # top of Algorithm 2's interval
+            a[:] = d["p"] - 1
+            t.copy_(torch.from_numpy(a.view(np.int32)).cuda())
+    for pl in b.plans.values():
+        pl.set_variant(ntt.VARIANT_NTL)
+    ntt.ntt_execute_uneven(b.descs())
+    torch.cuda.synchronize()
+    assert ntt.ntt_uneven_status() == 0
+    b.check()
+    plans = list(b.plans.values())
+    plans[0].set_variant(ntt.VARIANT_LAZY)
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_execute_uneven(b.descs())
+    assert e.value.code == -4
+    for pl in plans:
+        pl.set_variant(ntt.VARIANT_MONT)
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.ntt_execute_uneven(b.descs())
+    assert e.value.code == -9
+    for pl in plans:
+        pl.set_variant(ntt.VARIANT_LAZY)
