@@ -558,12 +558,13 @@ def run_uneven(args, dist, rank, world):
     }
 
 
-def run_serving(seconds, rate, torch, ntt, seed=5, max_log=20.0):
+def run_serving(seconds, rate, torch, ntt, seed=5, max_log=20.0, variant=0):
     """Poisson stream of polynomial products mod 998244353 (degrees
-    log-uniform in 2^6..2^max_log) through the continuous-batching server.
-    Operands are slices of one pinned pool of uniform residues; results go
-    to a pinned ring (not checked here; the tests check them).  Returns
-    latency percentiles and throughput."""
+    log-uniform in 2^6..2^max_log) through the continuous-batching server
+    (its transforms with the lazy butterflies, variant 0, or the NTL-style
+    ones, variant 1).  Operands are slices of one pinned pool of uniform
+    residues; results go to a pinned ring (not checked here; the tests check
+    them).  Returns latency percentiles and throughput."""
     from paper_1205_2926_gb300.inputs import serving_trace
     n = int(seconds * rate)
     trace = serving_trace(seed=seed, n=n, rate_per_s=rate, dmax_log=max_log)
@@ -573,7 +574,7 @@ def run_serving(seconds, rate, torch, ntt, seed=5, max_log=20.0):
     ring = torch.empty(ring_words, dtype=torch.int32).pin_memory()
     base, rbase = pool.data_ptr(), ring.data_ptr()
     sv = ntt.Server(P_NTT30, max_coeffs=(1 << int(max_log)) + 1, mem_budget_bytes=8 << 30, n_streams=8,
-                    max_batch=512)
+                    max_batch=512, variant=variant)
     rng = np.random.default_rng(seed)
     offs = rng.integers(0, pool_words - (1 << 21), size=(n, 2))
     # warm-up: one request of every length class
@@ -634,6 +635,8 @@ def run_serve_workload(args, dist, rank, world):
     t0 = time.time()
     res = run_serving(args.serve_seconds, 20000.0, torch, ntt)
     clocks = sampler.stop(t0, time.time())
+    # the same trace with the NTL-style butterflies (Algorithm 2)
+    res_ntl = run_serving(args.serve_seconds, 20000.0, torch, ntt, variant=1)
     # offered-load sweep around the configured rate (1 s each): where the
     # latency knee lies
     sweep = []
@@ -647,6 +650,8 @@ def run_serve_workload(args, dist, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded Poisson trace)",
         "config": {"workload": WORKLOADS["c5"]["name"], "seconds": args.serve_seconds},
         "serving": res, "rate_sweep": sweep, "clocks": clocks,
+        "ntl": {"p50_ms": res_ntl["p50_ms"], "p99_ms": res_ntl["p99_ms"],
+                "throughput_req_per_s": res_ntl["throughput_req_per_s"]},
     }
 
 
@@ -912,10 +917,13 @@ def run_ours(args, dist, rank, world):
             line["steady_256MiB"] = {"error": f"{type(e).__name__}: {e}"}
     if not args.no_serving and args.workload == "c2":
         sv = run_serving(args.serve_seconds, 20000.0, torch, ntt)
+        sv_ntl = run_serving(args.serve_seconds, 20000.0, torch, ntt, variant=1)
         detail["polymul_serving"] = sv
+        detail["polymul_serving_ntl"] = sv_ntl
         line["polymul_serving"] = {"seconds": args.serve_seconds, "offered_req_per_s": 20000,
                                    "p50_ms": round(sv["p50_ms"], 4), "p99_ms": round(sv["p99_ms"], 4),
-                                   "completed_req_per_s": round(sv["throughput_req_per_s"] or 0.0, 1)}
+                                   "completed_req_per_s": round(sv["throughput_req_per_s"] or 0.0, 1),
+                                   "ntl_p50_ms": round(sv_ntl["p50_ms"], 4), "ntl_p99_ms": round(sv_ntl["p99_ms"], 4)}
     if args.workload == "c2" and not args.no_u64:
         # the paper's own word size (beta = 2^64, Table 1): the 64-bit batched
         # configuration, lazy against NTL-style in the same schedule

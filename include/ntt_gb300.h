@@ -278,7 +278,7 @@ int ntt_transform_host(ntt_plan_t plan, int inverse, void *h_data, size_t batch,
 /* c = a * b in F_p[x] (the polynomial-multiplication application, Section 1):
  * zero-pad both operands to L = nextpow2(na + nb - 1), forward transforms,
  * pointwise product times L^-1 (Montgomery reduction as in Algorithm 5, then
- * a Shoup product by L^-1), inverse transform.  a, b, c are DEVICE arrays of
+ * a Shoup product by L^-1, reduced to [0, p)), inverse transform.  a, b, c are DEVICE arrays of
  * natural-order coefficients in [0, p) in the word type of p; c receives
  * na + nb - 1 words.  omega is the library's root for (p, L).  Plans are
  * cached per (device, p, L); device scratch of 2*L words is allocated per
@@ -458,6 +458,8 @@ typedef struct {
     size_t mem_budget_bytes; /* device bytes for admitted, unfinished requests */
     int n_streams;           /* concurrent CUDA streams, 1..64 */
     int max_batch;           /* most requests of one length per batch */
+    int variant;             /* butterflies of the server's transforms: NTT_VARIANT_LAZY (0, the
+                                default, Algorithms 3-4) or NTT_VARIANT_NTL (Algorithm 2) */
 } ntt_server_config_t;
 
 typedef struct {
@@ -470,7 +472,8 @@ typedef struct {
                                                 by kernels, with no per-request copy calls */
 } ntt_server_stats_t;
 
-/* Start a server on the current device.  Errors: NTT_ERR_ARG, NTT_ERR_MODULUS,
+/* Start a server on the current device.  Errors: NTT_ERR_ARG (also a variant
+ * other than LAZY or NTL), NTT_ERR_MODULUS,
  * NTT_ERR_LENGTH (p has no root of order nextpow2(2*max_coeffs-1)),
  * NTT_ERR_CUDA. */
 int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out);

@@ -252,8 +252,9 @@ def ntt_pass_set_wait_budget(cycles: int, stall_bytes: int = 0) -> None:
 class Server:
     """Continuous-batching polymul server (ntt_server_*); host arrays in and out."""
 
-    def __init__(self, p: int, max_coeffs: int, mem_budget_bytes: int, n_streams: int = 4, max_batch: int = 256):
-        cfg = _lib.ServerConfig(p, max_coeffs, mem_budget_bytes, n_streams, max_batch)
+    def __init__(self, p: int, max_coeffs: int, mem_budget_bytes: int, n_streams: int = 4, max_batch: int = 256,
+                 variant: int = 0):
+        cfg = _lib.ServerConfig(p, max_coeffs, mem_budget_bytes, n_streams, max_batch, variant)
         h = ctypes.c_void_p()
         check(_lib.load().ntt_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ntt_server_create")
         self.handle = h.value

@@ -33,7 +33,7 @@ class PlanInfo(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("p", c_u64), ("max_coeffs", c_size), ("mem_budget_bytes", c_size), ("n_streams", c_int),
-                ("max_batch", c_int)]
+                ("max_batch", c_int), ("variant", c_int)]
 
 
 class ServerStats(ctypes.Structure):

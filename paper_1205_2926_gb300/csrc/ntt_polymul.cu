@@ -34,7 +34,9 @@ template <typename W>
 __global__ void k_pointwise(W *__restrict__ A, const W *__restrict__ B, uint64_t L, W p, W J, W K, W Kq) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L; i += (uint64_t)gridDim.x * blockDim.x) {
         W y = mont_mul(A[i], B[i], J, p);
-        A[i] = shoup_mul(y, K, Kq, p);
+        // fully reduced: the inverse transform's input interval is [0, p)
+        // for the fully reduced butterflies (Algorithm 2)
+        A[i] = csub(shoup_mul(y, K, Kq, p), p);
     }
 }
 
@@ -49,15 +51,16 @@ static unsigned grid_for(uint64_t n) {
     return (unsigned)std::min<uint64_t>(g, 152 * 16);
 }
 
-// Plans cached per (device, p, L); kept for the life of the process.
+// Plans cached per (device, p, L, butterfly variant; -1 = the plan's
+// default); kept for the life of the process.
 static std::mutex g_cache_mu;
-static std::map<std::tuple<int, uint64_t, uint64_t>, ntt_plan_s *> g_cache;
+static std::map<std::tuple<int, uint64_t, uint64_t, int>, ntt_plan_s *> g_cache;
 
-int polymul_plan(uint64_t p, uint64_t L, ntt_plan_s **out) {
+int polymul_plan(uint64_t p, uint64_t L, ntt_plan_s **out, int variant) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto key = std::make_tuple(dev, p, L);
+    auto key = std::make_tuple(dev, p, L, variant);
     auto it = g_cache.find(key);
     if (it != g_cache.end()) {
         *out = it->second;
@@ -69,6 +72,13 @@ int polymul_plan(uint64_t p, uint64_t L, ntt_plan_s **out) {
     ntt_plan_t pl = nullptr;
     rc = ntt_plan(&pl, p, w, L);
     if (rc) return rc;
+    if (variant >= 0) {
+        rc = ntt_plan_set_variant(pl, variant);
+        if (rc) {
+            ntt_plan_destroy(pl);
+            return rc;
+        }
+    }
     g_cache[key] = pl;
     *out = pl;
     return NTT_OK;

@@ -13,8 +13,9 @@ namespace ntt {
 // Check (p, na, nb); on success *L_out = max(2, nextpow2(na + nb - 1)).
 int polymul_validate(uint64_t p, size_t na, size_t nb, uint64_t *L_out);
 
-// Cached plan for (current device, p, L) with the library's root of unity.
-int polymul_plan(uint64_t p, uint64_t L, ntt_plan_s **out);
+// Cached plan for (current device, p, L) with the library's root of unity,
+// set to butterfly variant `variant` (-1: the plan's default choice).
+int polymul_plan(uint64_t p, uint64_t L, ntt_plan_s **out, int variant = -1);
 
 // Enqueue A <- A B L^-1 mod p over L words (transforms in [0, 2p) from the
 // forward pass; result in [0, 2p), the inverse pass's input range).

@@ -46,7 +46,9 @@ template <typename W>
 __global__ void k_pointwise_batch(W *__restrict__ A, const W *__restrict__ B, uint64_t n, W p, W J, W K, W Kq) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         W y = mont_mul(A[i], B[i], J, p);
-        A[i] = shoup_mul(y, K, Kq, p);
+        // fully reduced: the inverse transform's input interval is [0, p)
+        // for the fully reduced butterflies (Algorithm 2)
+        A[i] = csub(shoup_mul(y, K, Kq, p), p);
     }
 }
 
@@ -303,7 +305,7 @@ static void scheduler(ntt_server_s *sv) {
             cudaEventCreateWithFlags(&bt.done, cudaEventDisableTiming);
             std::vector<Request *> rs;
             for (uint64_t id : bt.ids) rs.push_back(&sv->reqs[id]);
-            int rc = polymul_plan(sv->cfg.p, kv.first, &bt.plan);
+            int rc = polymul_plan(sv->cfg.p, kv.first, &bt.plan, sv->cfg.variant);
             if (rc == NTT_OK && sv->fail_next > 0) {
                 sv->fail_next--;
                 rc = NTT_ERR_FAILED;  // host-side failure injection
@@ -364,7 +366,7 @@ int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out) {
     *out = nullptr;
     if (cfg->p < 3 || cfg->p >= (1ull << 62) || !nt::is_prime(cfg->p)) return NTT_ERR_MODULUS;
     if (cfg->max_coeffs == 0 || cfg->mem_budget_bytes == 0 || cfg->n_streams < 1 || cfg->n_streams > 64 ||
-        cfg->max_batch < 1)
+        cfg->max_batch < 1 || (cfg->variant != NTT_VARIANT_LAZY && cfg->variant != NTT_VARIANT_NTL))
         return NTT_ERR_ARG;
     uint64_t L = 0;
     int rc = polymul_validate(cfg->p, cfg->max_coeffs, cfg->max_coeffs, &L);

@@ -191,3 +191,30 @@ def test_full_degree_range_through_the_gather_scatter_path():
             assert np.array_equal(tc.numpy().view(np.uint32).astype(np.uint64), want), (a.size, b.size)
     finally:
         sv.destroy()
+
+
+def test_ntl_variant_server_matches_oracle():
+    """A server whose transforms use the NTL-style butterflies (Algorithm 2):
+    every product equals the oracle's, including operands of all p - 1 (the
+    top of that butterfly's input interval); a variant it does not carry is
+    refused at creation."""
+    require_gpu()
+    reqs = make_requests(40, seed=23)
+    reqs[0] = (np.full(reqs[0][0].size, P_NTT30 - 1, dtype=np.uint32), np.full(reqs[0][1].size, P_NTT30 - 1, dtype=np.uint32))
+    sv = ntt.Server(P_NTT30, max_coeffs=1 << 15, mem_budget_bytes=256 << 20, n_streams=4, variant=ntt.VARIANT_NTL)
+    try:
+        outs = [np.zeros(a.size + b.size - 1, dtype=np.uint32) for a, b in reqs]
+        ids = []
+        for (a, b), c in zip(reqs, outs):
+            rc, rid = sv.submit(a.ctypes.data, a.size, b.ctypes.data, b.size, c.ctypes.data)
+            assert rc == 0
+            ids.append(rid)
+        assert sv.drain(60_000) == 0
+        assert all(sv.poll(r) == 0 for r in ids)
+        for (a, b), c in zip(reqs, outs):
+            assert np.array_equal(c.astype(np.uint64), expected(a, b))
+    finally:
+        sv.destroy()
+    with pytest.raises(ntt.NTTError) as e:
+        ntt.Server(P_NTT30, max_coeffs=1 << 10, mem_budget_bytes=64 << 20, variant=ntt.VARIANT_MONT)
+    assert e.value.code == -4
