@@ -577,10 +577,13 @@ def run_serving(seconds, rate, torch, ntt, seed=5, max_log=20.0, variant=0):
                     max_batch=512, variant=variant)
     rng = np.random.default_rng(seed)
     offs = rng.integers(0, pool_words - (1 << 21), size=(n, 2))
-    # warm-up: one request of every length class
+    # warm-up: one request of every length class, the largest included
+    # (operands of 2^max_log + 1 coefficients: L = 2^(max_log + 2))
     for lg in range(7, int(max_log) + 2):
         m = (1 << (lg - 1))
         sv.submit(base, m, base, m, rbase)
+    m = (1 << int(max_log)) + 1
+    sv.submit(base, m, base, m, rbase)
     sv.drain(-1)
     sv.reset_stats()
     # the submission loop replays the trace from plain lists, with Python's
@@ -648,7 +651,8 @@ def run_serve_workload(args, dist, rank, world):
         "metric": METRIC, "value": res["p99_ms"], "unit": "ms (p99 polymul latency)", "n_gpus": world,
         "steps": res["requests"], "warmup": args.warmup, "ms_per_step": res["mean_ms"], "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded Poisson trace)",
-        "config": {"workload": WORKLOADS["c5"]["name"], "seconds": args.serve_seconds},
+        "config": {"workload": WORKLOADS["c5"]["name"], "seconds": args.serve_seconds,
+                   "cuda_module_loading": os.environ.get("CUDA_MODULE_LOADING", "LAZY (default)")},
         "serving": res, "rate_sweep": sweep, "clocks": clocks,
         "ntl": {"p50_ms": res_ntl["p50_ms"], "p99_ms": res_ntl["p99_ms"],
                 "throughput_req_per_s": res_ntl["throughput_req_per_s"]},
@@ -1077,6 +1081,12 @@ def main():
         args.warmup = 3
     if args.serve_seconds is None:
         args.serve_seconds = 60.0 if args.workload == "c5" else 2.0
+    if args.workload == "c5":
+        # a serving process loads its CUDA modules at start-up: with the
+        # default lazy loading, 5 of 8 twenty-second runs at 20k req/s showed
+        # one 12-98 ms stall (and a p99 up to 23 ms); 0 of 8 with eager
+        # loading.  Set before the first CUDA call of the process.
+        os.environ.setdefault("CUDA_MODULE_LOADING", "EAGER")
     if "NTT_AUTOTUNE_CACHE" not in os.environ:
         # start from the pass splits tuned on this GPU model (shipped with the
         # package); a shape or GPU it lacks is tuned at run time into the copy

@@ -472,8 +472,10 @@ typedef struct {
                                                 by kernels, with no per-request copy calls */
 } ntt_server_stats_t;
 
-/* Start a server on the current device.  Errors: NTT_ERR_ARG (also a variant
- * other than LAZY or NTL), NTT_ERR_MODULUS,
+/* Start a server on the current device.  Makes the plan of every transform
+ * length it accepts (2 .. nextpow2(2 max_coeffs - 1)) before returning, so
+ * that no table upload or kernel load happens while requests are served.
+ * Errors: NTT_ERR_ARG (also a variant other than LAZY or NTL), NTT_ERR_MODULUS,
  * NTT_ERR_LENGTH (p has no root of order nextpow2(2*max_coeffs-1)),
  * NTT_ERR_CUDA. */
 int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out);

@@ -100,6 +100,9 @@ struct LaunchSpec {
 // persistent: geometry for the uneven-batch kernel (column tiles of at most
 // 2048 vectors, its two buffers); otherwise for k_pass.
 void tile_params(const ntt_plan_s *pl, int q, uint64_t batch, LaunchSpec &s, bool persistent = false);
+// kind: 0 column pass, 1 row pass, 2 tiny transform, 3 row pass with one
+// warp per row; KIND_PRELOAD loads every pass kernel of (word, dir, var).
+constexpr int KIND_PRELOAD = -1;
 cudaError_t launch_pass_u32(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
 cudaError_t launch_pass_u64(const LaunchSpec &s, int kind, int dir, int var, cudaStream_t st);
 

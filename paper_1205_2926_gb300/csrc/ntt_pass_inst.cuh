@@ -4,6 +4,7 @@
 #pragma once
 
 #include <algorithm>
+#include <mutex>
 
 #include "ntt_internal.hpp"
 #include "ntt_kernels.cuh"
@@ -41,17 +42,21 @@ static PassArgs<W> to_args(const LaunchSpec &s) {
 // Per kernel: shared-memory opt-in once per device, and the number of CTAs
 // that fit on one SM for the launch's shared-memory size (cached).  The
 // caches are per kernel instantiation (template arguments), not per
-// function type, which every k_pass of one word type shares.
+// function type, which every k_pass of one word type shares.  smem == 0:
+// the opt-in only (no launch has an empty shared-memory buffer).
 template <typename W, int DIR, int VAR, int LOGR, bool ROW>
 static cudaError_t kernel_slots(size_t smem, int *per_sm, int *sms) {
     auto kern = k_pass<W, DIR, VAR, LOGR, ROW>;
+    constexpr int kSizes = 8;  // shared-memory sizes remembered per device (round robin)
+    static std::mutex mu;
     static int configured[64] = {0};
-    static int cache_occ[64], cache_sms[64];
-    static size_t cache_smem[64];
+    static int cache_sms[64], cache_occ[64][kSizes], cache_next[64];
+    static size_t cache_smem[64][kSizes];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
     if (!configured[dev]) {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -61,18 +66,23 @@ static cudaError_t kernel_slots(size_t smem, int *per_sm, int *sms) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return e;
         cudaDeviceGetAttribute(&cache_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        cache_smem[dev] = (size_t)-1;
+        for (int i = 0; i < kSizes; ++i) cache_smem[dev][i] = (size_t)-1;
         configured[dev] = 1;
     }
-    if (cache_smem[dev] != smem) {
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
-        if (e != cudaSuccess) return e;
-        cache_occ[dev] = std::max(occ, 1);
-        cache_smem[dev] = smem;
-    }
-    *per_sm = cache_occ[dev];
+    if (smem == 0) return cudaSuccess;
     *sms = cache_sms[dev];
+    for (int i = 0; i < kSizes; ++i)
+        if (cache_smem[dev][i] == smem) {
+            *per_sm = cache_occ[dev][i];
+            return cudaSuccess;
+        }
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int slot = cache_next[dev]++ % kSizes;
+    cache_smem[dev][slot] = smem;
+    cache_occ[dev][slot] = std::max(occ, 1);
+    *per_sm = cache_occ[dev][slot];
     return cudaSuccess;
 }
 
@@ -136,8 +146,27 @@ static cudaError_t launch_warp_logr(const LaunchSpec &s, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+// Load (and configure) every pass kernel of one (word, direction, variant)
+// without launching it: under CUDA's lazy module loading a kernel is
+// otherwise loaded at its first launch.
+template <typename W, int DIR, int VAR, bool ROW, int LO, int HI>
+static cudaError_t preload_logr() {
+    int per_sm = 1, sms = 1;
+    cudaError_t e = kernel_slots<W, DIR, VAR, LO, ROW>(0, &per_sm, &sms);
+    if (e != cudaSuccess) return e;
+    if constexpr (LO < HI) return preload_logr<W, DIR, VAR, ROW, LO + 1, HI>();
+    return cudaSuccess;
+}
+
 template <typename W, int DIR, int VAR>
 static cudaError_t launch_kind(const LaunchSpec &s, int kind, cudaStream_t st) {
+    if (kind == KIND_PRELOAD) {
+        cudaError_t e = preload_logr<W, DIR, VAR, false, 3, kMaxColLog>();
+        if (e == cudaSuccess) e = preload_logr<W, DIR, VAR, true, 3, kMaxRowLog>();
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tiny<W, DIR, VAR>);
+        return e;
+    }
     if (kind == 3) return launch_warp_logr<W, DIR, VAR, 5, 10>(s, st);
     if (kind == 0) return launch_logr<W, DIR, VAR, false, 3, kMaxColLog>(s, s.logR, st);
     if (kind == 1) return launch_logr<W, DIR, VAR, true, 3, kMaxRowLog>(s, s.logR, st);

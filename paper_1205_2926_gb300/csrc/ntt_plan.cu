@@ -661,6 +661,20 @@ int ntt_find_prime(uint64_t lo, int k, uint64_t *q) {
     return NTT_ERR_RANGE;
 }
 
+// Load every pass kernel of the plan's word size and current variant, both
+// directions, at set-up time: under CUDA's lazy module loading a kernel is
+// otherwise loaded at its first launch, inside whatever latency-sensitive
+// call (a server batch, an allocation-free product) makes it.
+static int preload_kernels(const ntt_plan_s *pl) {
+    LaunchSpec s;
+    memset(&s, 0, sizeof(s));
+    for (int dir = 0; dir < 2; ++dir) {
+        cudaError_t e = launch(pl, s, KIND_PRELOAD, dir, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "kernel preload");
+    }
+    return NTT_OK;
+}
+
 int ntt_plan_words(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L, int word_bytes) {
     if (!out) return NTT_ERR_ARG;
     *out = nullptr;
@@ -700,6 +714,7 @@ int ntt_plan_words(ntt_plan_t *out, uint64_t p, uint64_t omega, uint64_t L, int 
     int logr[kMaxPasses];
     int n = default_split(pl->logL, pl->wbytes, logr);
     int rc = apply_split(pl, n, logr);
+    if (rc == NTT_OK) rc = preload_kernels(pl);
     if (rc) {
         free_tables(pl);
         delete pl;
@@ -731,8 +746,9 @@ int ntt_plan_set_variant(ntt_plan_t pl, int variant) {
         int rc = build_tables_form(pl, true);
         if (rc) return rc;
     }
+    const bool changed = pl->variant != variant;
     pl->variant = variant;
-    return NTT_OK;
+    return changed ? preload_kernels(pl) : NTT_OK;
 }
 
 int ntt_plan_get_info(ntt_plan_t pl, ntt_plan_info_t *info) {

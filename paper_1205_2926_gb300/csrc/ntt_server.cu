@@ -419,6 +419,35 @@ int ntt_server_create(const ntt_server_config_t *cfg, ntt_server_t *out) {
         }
         cudaGetLastError();  // a reservation that does not fit is not an error
     }
+    // the plan (twiddle tables, and with them the pass kernels) of every
+    // length class the server accepts, and the server's own kernels, made and
+    // loaded now: a plan made while requests are served allocates and
+    // uploads its tables and loads kernels, which stalls the batches in flight
+    {
+        cudaFuncAttributes fa;
+        cudaError_t e = sv->wbytes == 4 ? cudaFuncGetAttributes(&fa, k_gather<uint32_t>) : cudaFuncGetAttributes(&fa, k_gather<uint64_t>);
+        if (e == cudaSuccess)
+            e = sv->wbytes == 4 ? cudaFuncGetAttributes(&fa, k_scatter<uint32_t>) : cudaFuncGetAttributes(&fa, k_scatter<uint64_t>);
+        if (e == cudaSuccess)
+            e = sv->wbytes == 4 ? cudaFuncGetAttributes(&fa, k_pointwise_batch<uint32_t>)
+                                : cudaFuncGetAttributes(&fa, k_pointwise_batch<uint64_t>);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(sv->pool);
+            for (cudaStream_t t : sv->streams) cudaStreamDestroy(t);
+            delete sv;
+            return cuda_fail(e, "server kernels");
+        }
+    }
+    for (uint64_t l = 2; l <= L; l <<= 1) {
+        ntt_plan_s *pl = nullptr;
+        rc = polymul_plan(cfg->p, l, &pl, cfg->variant);
+        if (rc) {
+            cudaMemPoolDestroy(sv->pool);
+            for (cudaStream_t t : sv->streams) cudaStreamDestroy(t);
+            delete sv;
+            return rc;
+        }
+    }
     sv->worker = std::thread(scheduler, sv);
     *out = sv;
     return NTT_OK;
