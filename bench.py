@@ -728,7 +728,7 @@ STEADY = {
 }
 
 
-def steady_state(cases, torch, ntt, peak_gbs, K=20, warm=3, sm_mhz=2070.0):
+def steady_state(cases, torch, ntt, peak_gbs, K=20, warm=3, sm_mhz=2070.0, warp_rows=False):
     """The pass kernels at 256 MiB per batch (twice the L2, so every pass reads
     and writes HBM), CUDA-event time of K back-to-back launches of each pass.
     Per pass: that pass's bytes (one read and one write of every word) over its
@@ -736,13 +736,16 @@ def steady_state(cases, torch, ntt, peak_gbs, K=20, warm=3, sm_mhz=2070.0):
     (the algorithmic bytes of the whole transform, however many passes it
     takes) over the forward+inverse time, against the measured HBM copy peak;
     and butterflies/s against the integer-multiply roof.  The split is the
-    library's own for that batch (autotuned, cached)."""
+    library's own for that batch (autotuned, cached); with warp_rows the row
+    passes of 2^5..2^10 words run with one warp per row."""
     out = []
     for p, l, b in cases:
         L = 1 << l
         w = 4 if p < (1 << 30) else 8
         plan = ntt.ntt_plan(p, ntt.root_of_unity(p, L), L)
         split = plan.autotune(b, use_cache=True)
+        if warp_rows:
+            plan.set_warp_rows(True)
         a = batch_inputs(3, b, L, p)
         t = torch.from_numpy(a.view(np.int32) if w == 4 else a.view(np.int64)).cuda()
         passes, total_us = [], 0.0
@@ -791,9 +794,9 @@ def run_steady_only(args):
     K = max(1, args.steady_launches)
     cases = STEADY.get(args.workload, STEADY["c2"])
     return {"what": "pass kernels at 256 MiB per pass, CUDA events, HBM fraction of measured peak",
-            "launches_per_pass": K,
+            "launches_per_pass": K, "row_body": "one warp per row" if args.warp_rows else "radix-8 CTA rows",
             "cases": steady_state(cases, torch, ntt, load_peaks()["hbm_gbs"], K=K, warm=3 if K > 1 else 0,
-                                  sm_mhz=load_peaks()["sm_max_mhz"])}
+                                  sm_mhz=load_peaks()["sm_max_mhz"], warp_rows=args.warp_rows)}
 
 
 def run_ours(args, dist, rank, world):
@@ -1074,6 +1077,8 @@ def main():
     ap.add_argument("--no-steady-state", action="store_true", help="skip the 256 MiB per-pass report")
     ap.add_argument("--steady-only", action="store_true",
                     help="only the 256 MiB per-pass report (for profiling the pass kernels at that size)")
+    ap.add_argument("--warp-rows", action="store_true",
+                    help="with --steady-only: row passes of 2^5..2^10 words with one warp per row")
     ap.add_argument("--steady-launches", type=int, default=20,
                     help="timed launches per pass in the 256 MiB report (1: no warm-up, one launch per pass)")
     args = ap.parse_args()
