@@ -12,8 +12,9 @@
 // previous one wrote shortly before (from L2), with the single-pass items
 // spread over the steps.
 //
-// Device side: each CTA of the persistent grid takes the next item from an
-// atomic counter.  An item of stage s > 0 waits until every item of stage
+// Device side (ntt_uneven_kernel.cuh; one kernel per butterfly variant,
+// compiled in ntt_uneven_lazy.cu and ntt_uneven_ntl.cu): each CTA of the
+// persistent grid takes the next item from an atomic counter.  An item of stage s > 0 waits until every item of stage
 // s-1 of its task has finished (a per-(task, stage) completion counter).  It
 // only ever waits for items with a smaller index, which were taken by CTAs
 // already running, so the waits cannot deadlock whatever the residency.
